@@ -1,0 +1,200 @@
+"""Step-level pins of the FP64 oracle (CPU only):
+
+* free-stream preservation (consistency of f_S and zero row sums of D);
+* exact conservation of the domain totals (SBP telescoping of the time-averaged
+  fluxes, eqs. crkfr.non.cons.final and numflux.cons), 1e-13 over 100 steps;
+* design-order convergence on the smooth periodic density wave (exact solution
+  rho(x - t)), order >= N + 1/2 (Sec. 4.1 reports convergence tests);
+* the multi-D tensor-product reading reduces to the 1D scheme for data that
+  vary in x only;
+* the linearised one-step map is stable (spectral radius <= 1) at the CFL
+  numbers chosen per degree.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_02125_gb300 import inputs
+
+
+def _const_state(mesh, seed=0):
+    M = inputs.nvars(mesh)
+    E, npe = inputs.num_elems(mesh), inputs.nodes_per_elem(mesh)
+    rng = np.random.default_rng(seed)
+    if mesh["eq"] == "euler":
+        dim = mesh["dim"]
+        rho, p = 1.3, 0.9
+        v = rng.uniform(-0.5, 0.5, dim)
+        u = [rho] + list(rho * v) + [p / (mesh["gamma"] - 1) + 0.5 * rho * v @ v]
+    else:
+        rho, p, v, B, psi = 1.1, 0.8, np.array([0.3, -0.2, 0.1]), np.array([0.4, 0.5, -0.3]), 0.05
+        u = [rho, *(rho * v), p / (mesh["gamma"] - 1) + 0.5 * rho * v @ v + 0.5 * B @ B + 0.5 * psi ** 2, *B, psi]
+    U = np.empty((M, E, npe))
+    for k in range(M):
+        U[k] = u[k]
+    return U
+
+
+@pytest.mark.parametrize("eq,dim,N,vol", [("euler", 1, 3, "ec"), ("euler", 2, 3, "kep"), ("euler", 3, 2, "ec"),
+                                          ("glm_mhd", 2, 4, "ec"), ("euler", 2, 5, "ec"), ("euler", 1, 1, "ec")])
+def test_free_stream(orc, eq, dim, N, vol):
+    if eq == "euler":
+        mesh = inputs.mesh_dict(eq, dim, N, [3] * dim, [0] * dim, [1.0] * dim, 1.4, vol=vol)
+    else:
+        mesh = inputs.mesh_dict(eq, 2, N, [3, 3], [0, 0], [1, 1], 5.0 / 3.0, vol=vol, c_h=1.5)
+    U = _const_state(mesh)
+    dt = orc.cfl_dt(mesh, U)
+    U1 = orc.step(mesh, U, dt)
+    np.testing.assert_allclose(U1, U, rtol=1e-13, atol=1e-13)
+
+
+def _weights(mesh, orc):
+    xi, w, *_ = orc.tables(mesh["N"])
+    n = mesh["N"] + 1
+    dim = mesh["dim"]
+    W = np.ones(n ** dim)
+    for p in range(n ** dim):
+        rem = p
+        for _ in range(dim):
+            W[p] *= w[rem % n]
+            rem //= n
+    return W
+
+
+def _totals(mesh, U, W):
+    vol = np.prod([(mesh["hi"][k] - mesh["lo"][k]) / mesh["cells"][k] for k in range(mesh["dim"])])
+    return vol * np.einsum("vep,p->v", U, W), vol * np.einsum("vep,p->v", np.abs(U), W)
+
+
+@pytest.mark.parametrize("case", ["shear", "tgv", "mhd", "wave_kep"])
+def test_conservation_100_steps(orc, case):
+    if case == "shear":
+        mesh, U = inputs.shear_layer_2d(cells=(6, 6), N=3)
+        cons = range(4)
+    elif case == "tgv":
+        mesh, U = inputs.tgv_3d(cells=(3, 3, 3), N=2, mach=0.3)
+        cons = range(5)
+    elif case == "wave_kep":
+        mesh, U = inputs.density_wave_1d(cells=10, N=4, vol="kep", cfl=0.07)
+        cons = range(3)
+    else:
+        mesh, U = inputs.mhd_vortex_2d(cells=(4, 4), N=3)
+        cons = [0]          # the Powell / GLM terms are non-conservative
+    nsteps = 100 if case != "tgv" else 30
+    W = _weights(mesh, orc)
+    T0, A0 = _totals(mesh, U, W)
+    U1, _ = orc.run(mesh, U, nsteps)
+    T1, _ = _totals(mesh, U1, W)
+    _, A1 = _totals(mesh, np.abs(U1), W)
+    for v in cons:
+        denom = max(abs(T0[v]), A0[v], A1[v])
+        if denom == 0.0:
+            assert T1[v] == 0.0
+            continue
+        assert abs(T1[v] - T0[v]) / denom < 1e-13, (v, T0[v], T1[v])
+    # the oracle's own FP64 totals agree with the quadrature sums above
+    np.testing.assert_allclose(orc.totals(mesh, U1)[:len(T1)], T1, rtol=1e-12, atol=1e-12)
+
+
+def _wave_error(orc, cells, N, vol, T=0.5):
+    mesh, U = inputs.density_wave_1d(cells=cells, N=N, vol=vol)
+    dx = 2.0 / cells
+    dt_cfl = inputs.default_cfl(N) * dx / 3.0
+    nsteps = int(np.ceil(T / dt_cfl))
+    U1, _ = orc.run(mesh, U, nsteps, dt_fixed=T / nsteps)
+    ex = inputs.density_wave_exact_1d(mesh, T)
+    xi, w, *_ = orc.tables(N)
+    return np.sqrt(np.sum((U1[0] - ex) ** 2 * w[None, :]) * dx)
+
+
+@pytest.mark.parametrize("N,vol,cells", [(1, "ec", (16, 32, 64)), (2, "ec", (8, 16, 32)), (3, "ec", (8, 16, 32)),
+                                         (3, "kep", (8, 16, 32)), (4, "ec", (4, 8, 16)), (5, "ec", (4, 8, 12))])
+def test_density_wave_convergence(orc, N, vol, cells):
+    errs = [_wave_error(orc, c, N, vol) for c in cells]
+    rates = [np.log(errs[i] / errs[i + 1]) / np.log(cells[i + 1] / cells[i]) for i in range(len(cells) - 1)]
+    # EC flux: design order N+1; the KEP (Kennedy-Gruber) flux averages e = E/rho,
+    # which perturbs the pressure of this wave at O(h^N): order N (the formal order
+    # of flux differencing with a general two-point flux; Sec. 4.1 also reports a
+    # sub-optimal order for KEP on GLL nodes)
+    assert rates[-1] >= (N + 0.5 if vol == "ec" else N), (errs, rates)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_multid_reduces_to_1d(orc, dim):
+    N = 3
+    mesh1, U1d = inputs.density_wave_1d(cells=6, N=N)
+    meshd = inputs.mesh_dict("euler", dim, N, [6] + [2] * (dim - 1), [0.0] * dim, [2.0] + [0.7] * (dim - 1), 1.4)
+    X = inputs.node_coords(meshd)
+    rho = 1.0 + 0.5 * np.sin(np.pi * X[0])
+    zero = np.zeros_like(rho)
+    U = inputs.euler_cons(1.4, rho, [np.ones_like(rho)] + [zero] * (dim - 1), np.ones_like(rho))
+    dt = 0.01
+    for _ in range(3):
+        U1d = orc.step(mesh1, U1d, dt)
+        U = orc.step(meshd, U, dt)
+    n = N + 1
+    E = inputs.num_elems(meshd)
+    for e in range(E):
+        ex = e % 6
+        for p in range(n ** dim):
+            i = p % n
+            for v, v1 in [(0, 0), (1, 1), (dim + 1, 2)]:
+                assert abs(U[v, e, p] - U1d[v1, ex, i]) < 1e-13
+            for v in range(2, dim + 1):
+                assert abs(U[v, e, p]) < 1e-14
+
+
+def _scalar_advection_model(orc, N, cfl, E=5):
+    """Amplification matrix of cRK-FR for u_t + u_x = 0 with the upwind flux,
+    written from the linear structure of the scheme: inner stages use only the
+    element-local operator, the final update applies the full FR operator to
+    the time average U = sum_i b_i u^(i) (for a linear flux F = a U)."""
+    xi, w, D, dgL, dgR = orc.tables(N)
+    A, b = orc.butcher(N)
+    n = N + 1
+    dx = 1.0 / E
+    Lloc = np.zeros((E * n, E * n))
+    L = np.zeros((E * n, E * n))
+    for e in range(E):
+        Lloc[e * n:(e + 1) * n, e * n:(e + 1) * n] = -D / dx
+    L[:] = Lloc
+    for e in range(E):
+        im, ip = e * n + N, ((e + 1) % E) * n
+        # upwind: F^num = U^-; jumps F^num - F^- = 0 on the left element,
+        # F^num - F^+ = U^- - U^+ on the right element, times d_x g_L
+        L[ip, im] += -dgL[0] / dx
+        L[ip, ip] += dgL[0] / dx
+    dt = cfl * dx
+    I = np.eye(E * n)
+    P = [I]
+    for i in range(1, len(b)):
+        P.append(I + dt * sum(A[i, j] * (Lloc @ P[j]) for j in range(i)))
+    G = I + dt * L @ sum(b[i] * P[i] for i in range(len(b)))
+    return np.max(np.abs(np.linalg.eigvals(G)))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_linear_stability_at_cfl(orc, N):
+    """Spectral radius of the linearised step around a constant state (central
+    finite differences of the oracle step) at dt = CFL dx / lambda_max.  The
+    fastest characteristic is advected at exactly the CFL number with an upwind
+    Rusanov flux, so the spectral radius equals that of the scalar model.
+    At N <= 3 the step is stable to round-off; at N = 4, 5 order-5/6 cRK has a
+    weak growth that no choice of tableau of that order removes (it is fixed by
+    the order conditions): about 8e-7 (N=4, CFL 0.07) and 4e-5 (N=5, CFL 0.05)
+    per step."""
+    mesh = inputs.mesh_dict("euler", 1, N, [5], [0.0], [1.0], 1.4)
+    U0 = _const_state(mesh, seed=3)
+    dt = orc.cfl_dt(mesh, U0)
+    n = U0.size
+    J = np.zeros((n, n))
+    h = 1e-5
+    for k in range(n):
+        dU = np.zeros(n)
+        dU[k] = h
+        J[:, k] = (orc.step(mesh, (U0.ravel() + dU).reshape(U0.shape), dt).ravel()
+                   - orc.step(mesh, (U0.ravel() - dU).reshape(U0.shape), dt).ravel()) / (2 * h)
+    rho = np.max(np.abs(np.linalg.eigvals(J)))
+    model = _scalar_advection_model(orc, N, inputs.default_cfl(N))
+    assert abs(rho - model) < 1e-8, (rho, model)   # central-difference error ~1e-9
+    bound = {1: 1e-9, 2: 1e-9, 3: 1e-9, 4: 1e-6, 5: 5e-5}[N]
+    assert rho <= 1.0 + bound, rho
