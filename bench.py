@@ -1,0 +1,290 @@
+"""Benchmark of the cRKFR hot path on one GB300 (DOF-updates/s).
+
+A "step" is one cRKFR time step (volume kernel + face/update kernel) of the
+2D Euler shear layer on 256 x 256 quads, N = 3 (1,048,576 nodes), with FP32
+pair fluxes and the FP64 state update (the headline form).  Each timed step
+is bracketed by CUDA events on the solver's stream; between timed steps a
+256 MiB buffer is written to flush the 129 MB L2 (the step's working set,
+about 110 MB, would otherwise stay L2-resident).
+
+Also reported: the plain FP64 form on the same workload (fewer steps), the
+end-to-end rate through the C ABI with host buffers (copies inside the timed
+region), the volume kernel's roofline fraction, SM clocks sampled during the
+timed region, and the FP64 CPU oracle timed on the host cores on a bounded
+sample of the workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 (torchrun) every rank advances its own replica (the method needs
+no exchange between independent replicas): weak scaling, max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cRKFR DOF-updates/s (FP32-flux & batched vs plain FP64, 1 GB300) at stated L2 error"
+WORKLOAD = "2D compressible Euler shear layer, periodic [-1,1]^2, 256x256 quads, N=3, EC (Ranocha) flux, Rusanov"
+CELLS = (256, 256)
+N_DEG = 3
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# Algorithmic FP32 work of the volume kernel (counted from the formulas; an FMA
+# is two flops, a reciprocal or logarithm one): per Ranocha pair flux in 2D,
+# two logarithmic means (series branch, 18 + 17), averages and the flux
+# (22), and the accumulation into both nodes (2 x M FMA = 16): 73 flops.
+# Per node and stage: pair data (12), stage combination (2 M), residual
+# scaling (2 M): 28 flops.
+FLOPS_PER_PAIR_2D = 73
+FLOPS_PER_NODE_STAGE_2D = 28
+
+
+def volume_flops_2d(E, N, stages):
+    n = N + 1
+    pairs = E * stages * 2 * n * (n * (n - 1) // 2)
+    nodes = E * n * n
+    return pairs * FLOPS_PER_PAIR_2D + nodes * stages * FLOPS_PER_NODE_STAGE_2D
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling (200 ms) around a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join(ROOT, ".clocks_%d.csv" % os.getpid()), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        name = self.out.name
+        self.out.close()
+        os.remove(name)
+        sm, mx, reasons = [], [], set()
+        keys = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, v in zip(keys, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(k)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_steps(solver, steps, stream, flush):
+    """Per-step CUDA-event time (ms) of `steps` solver steps, L2 flushed between."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        solver.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cpu_baseline(sample_cells=(128, 128), steps=6):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_2604_02125_gb300 import inputs
+    oracle.build()
+    mesh, U = inputs.shear_layer_2d(cells=sample_cells, N=N_DEG)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = oracle.step(mesh, U, oracle.cfl_dt(mesh, U))
+    dtw = time.perf_counter() - t0
+    nodes = inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
+    return {"value": nodes * steps / dtw, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the same shear layer on %dx%d quads, N=%d (%d nodes), single thread, %.1f s"
+                      % (steps, sample_cells[0], sample_cells[1], N_DEG, nodes, dtw)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2604_02125_gb300 import inputs
+    oracle.build()
+    cells = (24, 24)
+    mesh, U = inputs.shear_layer_2d(cells=cells, N=N_DEG)
+    for _ in range(args.warmup):
+        U = oracle.step(mesh, U, oracle.cfl_dt(mesh, U))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = oracle.step(mesh, U, oracle.cfl_dt(mesh, U))
+    el = time.perf_counter() - t0
+    nodes = inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
+    value = nodes * args.steps / el
+    sample = ("each step: one oracle step of the shear layer on %dx%d quads, N=%d (%d nodes), FP64, single thread"
+              % (cells[0], cells[1], N_DEG, nodes))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (bounded CPU sample, %dx%d quads)" % cells, "form": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2604_02125_gb300 import build, crkfr, inputs
+    build.build()
+    mesh, U = inputs.shear_layer_2d(cells=CELLS, N=N_DEG)
+    E = inputs.num_elems(mesh)
+    nodes = E * inputs.nodes_per_elem(mesh)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        s32 = crkfr.Solver(mesh, prec="fp32", stream=stream)
+        s32.set_state(U)
+        s32.step(args.warmup)
+        s32.sync()
+        clk = ClockSampler(local)
+        clk.start()
+        barrier()
+        times = time_steps(s32, args.steps, stream, flush)
+        barrier()
+        clocks = clk.stop()
+        status = s32.info()["status"]
+        total_ms = sum(times)
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * nodes * args.steps / (total_ms * 1e-3)
+
+        # plain FP64 form, same workload, a few steps
+        k64 = max(3, min(30, args.steps))
+        s64 = crkfr.Solver(mesh, prec="fp64", stream=stream)
+        s64.set_state(U)
+        s64.step(2)
+        s64.sync()
+        t64 = time_steps(s64, k64, stream, flush)
+        s64.close()
+
+        # volume-kernel duration, CUDA events on the solver's stream, same L2 flush
+        kv = max(3, min(50, args.steps))
+        vol_ms, face_ms = s32.time_kernels(kv, flush)
+
+        # end to end through the C ABI with host buffers
+        Uh = torch.from_numpy(U).pin_memory()
+        Oh = torch.empty_like(Uh).pin_memory()
+        ke = max(3, min(20, args.steps))
+        s32.set_state(Uh)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            s32.set_state(Uh)
+            s32.step(1)
+            s32.get_state(Oh)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        s32.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    stages = 4
+    vflops = volume_flops_2d(E, N_DEG, stages)
+    peaks = _peaks()
+    sm_mhz_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz_max * 1e6 / 1e12     # TFLOP/s, FP32 FMA lanes x clock
+    ms_step = total_ms / args.steps
+    roofline = None
+    if vol_ms:
+        ach = vflops / (vol_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                    "traffic": None, "kernel": "k_volume<Euler<2>,3,float>", "ms_per_launch": vol_ms,
+                    "face_update_ms_per_launch": face_ms}
+    out = {
+        "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "fp32 pair fluxes, fp64 update", "elements": E, "nodes": nodes,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "gpu_launches": 2 * args.steps,
+        "status": crkfr.status_string(status),
+        "forms": {"fp32_pairflux": {"value": value, "ms_per_step": ms_step},
+                  "fp64": {"value": nodes * k64 / (sum(t64) * 1e-3), "ms_per_step": sum(t64) / k64, "steps": k64}},
+        "e2e": {"value": world * nodes * ke / e2e_s, "unit": "DOF-updates/s",
+                "h2d_bytes_per_step": int(U.nbytes), "d2h_bytes_per_step": int(U.nbytes)},
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/*
+ * cr.h -- C ABI of the GB300 (sm_103a) cRKFR library.
+ *
+ * The library advances the semi-discrete system
+ *     u_t + f(u)_x + B(u) g(u)_x = 0            (paper: eq. flux.and.non.cons, Sec. 2)
+ * by the compact Runge-Kutta flux reconstruction method with flux-differencing
+ * volume terms (Sec. 3): per step, element-local cRK stages (eq. crkfr.inner)
+ * with the two-point volume flux (eq. entropy.cons.flux.dev) and the
+ * non-symmetric non-conservative product (eq. entropy.cons.noncons.dev), the
+ * time-averaged flux and solution (eq. disc.avg.flux), one Rusanov flux per
+ * face node (eq. numflux.cons) with the reduced-communication
+ * non-conservative flux B(u^{n,+-}) g^avg(U) (Sec. 2.3), and the final update
+ * (eq. crkfr.non.cons.final) followed by the CFL time step reduction.
+ *
+ * Meshes are uniform periodic Cartesian grids of tensor-product elements with
+ * GLL solution points on the reference element [0,1] (Sec. 2).
+ *
+ * State layout (all entry points): FP64 conserved variables, structure of
+ * arrays [var][elem][node]; node index (i, j, k) flattened with i fastest,
+ * element index (ex, ey, ez) flattened with ex fastest.  Variables:
+ *   Euler (dim d):  rho, rho v_1..rho v_d, E         (M = d + 2)
+ *   ideal GLM-MHD:  rho, rho v_1..3, E, B_1..3, psi  (M = 9, dim 2 only)
+ *   E = p/(gamma-1) + rho|v|^2/2 [+ |B|^2/2 + psi^2/2].
+ *
+ * Every function returns an int status (CR_OK = 0, negative on error) and
+ * never aborts or traps.  Errors leave the context usable unless stated.
+ */
+#ifndef CR_H
+#define CR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CR_OK            0
+#define CR_EINVAL       (-1)   /* invalid argument or descriptor                       */
+#define CR_ENOMEM       (-2)   /* device allocation failed                             */
+#define CR_ECUDA        (-3)   /* a CUDA runtime call failed                           */
+#define CR_ENONPHYSICAL (-4)   /* a step produced rho <= 0, p <= 0 or a non-finite value */
+#define CR_ETIMEOUT     (-5)   /* a bounded device wait (batched grid barrier) expired  */
+#define CR_ENODEV       (-6)   /* no usable CUDA device / wrong architecture           */
+
+/* system (eq. flux.and.non.cons) */
+#define CR_EULER   0           /* compressible Euler, dim 1..3                         */
+#define CR_GLM_MHD 1           /* ideal GLM-MHD with Powell/GLM non-conservative terms, dim 2 */
+
+/* two-point volume flux f_S (Sec. 3) */
+#define CR_VOL_EC      0       /* Euler: Ranocha (EC + KEP); GLM-MHD: entropy conservative */
+#define CR_VOL_KEP     1       /* Euler: Kennedy-Gruber (KEP, arithmetic means)         */
+#define CR_VOL_CENTRAL 2       /* (f(u_p)+f(u_q))/2: reduces to collocation D f         */
+
+/* surface flux (eq. numflux.cons) */
+#define CR_SURF_RUSANOV 0
+
+/* arithmetic of the element-local work */
+#define CR_FP64          0     /* every step of the path in FP64                        */
+#define CR_FP32_PAIRFLUX 1     /* stages, pair fluxes, time averages and face fluxes in
+                                  FP32; the state update u^{n+1} = u^n - dt(...), the dt
+                                  reduction and the diagnostic totals stay FP64          */
+
+typedef struct {
+  int eq;            /* CR_EULER | CR_GLM_MHD                                           */
+  int dim;           /* 1, 2, 3 (GLM-MHD: 2)                                            */
+  int degree_N;      /* polynomial degree N = 1..5 (N+1 GLL points per direction)        */
+  int cells[3];      /* elements per direction; entries beyond dim are ignored           */
+  double lo[3], hi[3];  /* periodic box                                                 */
+  double gamma;      /* ratio of specific heats                                         */
+  double cfl;        /* dt = cfl / max_nodes sum_d lambda_d / dx_d                       */
+  double c_h;        /* GLM cleaning speed (GLM-MHD only), fixed for the run             */
+  double dt_fixed;   /* > 0: use this dt every step instead of the CFL rule              */
+  int vol;           /* CR_VOL_*                                                        */
+  int surf;          /* CR_SURF_RUSANOV                                                 */
+  int prec;          /* CR_FP64 | CR_FP32_PAIRFLUX                                      */
+} cr_mesh_desc;
+
+typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
+
+/* Create a context on the current CUDA device.
+ *   out        : receives the context (NULL on failure).
+ *   desc       : n_solves descriptors (copied).
+ *   n_solves   : 1 = one mesh advanced by three kernels per step (volume, face +
+ *                update, replayed as a CUDA graph); > 1 = batched form: all
+ *                solves advance together in one persistent kernel per step
+ *                (requires prec = CR_FP32_PAIRFLUX, eq = CR_EULER, dim = 2).
+ *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
+ * The library allocates and owns all device buffers (state, stage/trace
+ * scratch, reduction partials).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
+
+/* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */
+int cr_state_size(const cr_ctx *ctx, int solve, int *n_vars, long long *n_nodes);
+
+/* Copy a state in (layout above; n_vars x n_nodes doubles).  u is a host
+ * pointer (u_on_device = 0; pageable or pinned) or a device pointer on the
+ * context's device (u_on_device = 1).  The caller keeps ownership.  Resets
+ * t = 0 and the step counter, checks physicality (CR_ENONPHYSICAL) and
+ * computes the first time step.  Synchronises the stream. */
+int cr_set_state(cr_ctx *ctx, int solve, const double *u, int u_on_device);
+
+/* Enqueue nsteps time steps on the stream (asynchronous; no host sync).
+ * A non-physical result is reported by the next cr_sync / cr_get_state /
+ * cr_get_info.  Returns CR_EINVAL for nsteps < 0 or a context without state. */
+int cr_step(cr_ctx *ctx, int nsteps);
+
+/* Wait for the stream and return the accumulated device status
+ * (CR_OK, CR_ENONPHYSICAL, CR_ETIMEOUT) or CR_ECUDA. */
+int cr_sync(cr_ctx *ctx);
+
+/* Copy the state of a solve out (same layout and pointer rules as
+ * cr_set_state).  Synchronises the stream; returns the device status. */
+int cr_get_state(cr_ctx *ctx, int solve, double *u, int u_on_device);
+
+/* Time, last time step, steps taken and (if totals != NULL) FP64
+ * quadrature-weighted domain totals: totals[0..M-1] conserved variables,
+ * totals[M] kinetic energy, totals[M+1] entropy -rho s/(gamma-1),
+ * s = ln p - gamma ln rho.  Synchronises the stream. */
+int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps, double *totals);
+
+/* Measurement: advance nsteps more steps with each kernel launched directly
+ * (not from the graph) between CUDA events recorded on the context's stream;
+ * before every step, if flush_buf != NULL, flush_bytes of that device buffer
+ * are overwritten (cudaMemsetAsync) to evict the L2.  ms[0] receives the mean
+ * duration of one volume-kernel launch, ms[1] of one face/update launch (the
+ * batched form: ms[0] = one persistent step launch, ms[1] = 0).  The state
+ * advances exactly as with cr_step.  Synchronises the stream. */
+int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
+
+/* Release every device buffer and graph of the context. */
+int cr_destroy(cr_ctx *ctx);
+
+/* Static description of a status code. */
+const char *cr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CR_H */

@@ -1,0 +1,220 @@
+"""Thin Python binding of the C ABI in include/cr.h (argument marshalling only).
+
+Every step of the cRKFR path runs in the CUDA library libcrkfr.so; this module
+only builds descriptors and passes pointers.  PyTorch is used, when given, for
+device memory (tensor data pointers) and streams.  There is no CPU fallback:
+if the compiled library is missing, :func:`load_library` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcrkfr.so")
+
+CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENONPHYSICAL, CR_ETIMEOUT, CR_ENODEV = 0, -1, -2, -3, -4, -5, -6
+EQ = {"euler": 0, "glm_mhd": 1}
+VOL = {"ec": 0, "kep": 1, "central": 2}
+SURF = {"rusanov": 0}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class CrError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("eq", ctypes.c_int), ("dim", ctypes.c_int), ("degree_N", ctypes.c_int),
+                ("cells", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("vol", ctypes.c_int), ("surf", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+_lib = None
+
+EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
+           "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string")
+
+
+def load_library(path=None):
+    """Load libcrkfr.so (built by paper_2604_02125_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("the CUDA library %s is not built; run paper_2604_02125_gb300.build.build()" % p)
+    lib = ctypes.CDLL(p)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.cr_init_mesh.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MeshDesc), ip, vp]
+    lib.cr_state_size.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    lib.cr_set_state.argtypes = [vp, ip, vp, ip]
+    lib.cr_step.argtypes = [vp, ip]
+    lib.cr_sync.argtypes = [vp]
+    lib.cr_get_state.argtypes = [vp, ip, vp, ip]
+    lib.cr_get_info.argtypes = [vp, ip, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp]
+    lib.cr_time_kernels.argtypes = [vp, ip, vp, ctypes.c_size_t, dp]
+    lib.cr_destroy.argtypes = [vp]
+    lib.cr_status_string.argtypes = [ip]
+    lib.cr_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "cr_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_string(s):
+    try:
+        return load_library().cr_status_string(int(s)).decode()
+    except RuntimeError:
+        return "status %d" % s
+
+
+def make_desc(mesh, prec="fp64", dt_fixed=0.0):
+    d = MeshDesc()
+    d.eq = EQ[mesh.get("eq", "euler")]
+    d.dim = mesh["dim"]
+    d.degree_N = mesh["N"]
+    cells = list(mesh["cells"]) + [1] * 3
+    lo = list(mesh["lo"]) + [0.0] * 3
+    hi = list(mesh["hi"]) + [1.0] * 3
+    for k in range(3):
+        d.cells[k], d.lo[k], d.hi[k] = int(cells[k]), float(lo[k]), float(hi[k])
+    d.gamma = mesh.get("gamma", 1.4)
+    d.cfl = mesh.get("cfl", 0.1)
+    d.c_h = mesh.get("c_h", 0.0)
+    d.dt_fixed = float(dt_fixed)
+    d.vol = VOL[mesh.get("vol", "ec")]
+    d.surf = SURF[mesh.get("surf", "rusanov")]
+    d.prec = PREC[prec]
+    return d
+
+
+def _check(rc, what):
+    if rc != CR_OK:
+        raise CrError(rc, what)
+
+
+def _ptr_and_location(a):
+    """(pointer, on_device) of a C-contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("state arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    import torch  # noqa: F401  (only for tensors)
+    if a.dtype != __import__("torch").float64 or not a.is_contiguous():
+        raise ValueError("state tensors must be contiguous float64")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+class Solver:
+    """One mesh (mesh dict) or a batch of meshes (list of mesh dicts).
+
+    prec: 'fp64' (plain path) or 'fp32' (FP32 pair fluxes, FP64 update).
+    stream: a cudaStream_t handle (int) or a torch.cuda.Stream; default: the
+    current torch stream if torch has initialised CUDA, else the legacy stream.
+    """
+
+    def __init__(self, mesh, prec="fp64", dt_fixed=0.0, stream=None):
+        self.lib = load_library()
+        meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
+        self.meshes = list(meshes)
+        arr = (MeshDesc * len(meshes))(*[make_desc(m, prec, dt_fixed) for m in meshes])
+        self._descs = arr
+        if stream is None:
+            stream = _current_torch_stream()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream or 0)
+        h = ctypes.c_void_p()
+        _check(self.lib.cr_init_mesh(ctypes.byref(h), arr, len(meshes), ctypes.c_void_p(self.stream)),
+               "cr_init_mesh")
+        self.h = h
+
+    def state_size(self, solve=0):
+        nv = ctypes.c_int()
+        nn = ctypes.c_longlong()
+        _check(self.lib.cr_state_size(self.h, solve, ctypes.byref(nv), ctypes.byref(nn)), "cr_state_size")
+        return nv.value, nn.value
+
+    def set_state(self, u, solve=0):
+        ptr, dev = _ptr_and_location(u)
+        M, nodes = self.state_size(solve)
+        count = u.size if isinstance(u, np.ndarray) else u.numel()
+        if count != M * nodes:
+            raise ValueError("state has %d values, expected %d" % (count, M * nodes))
+        _check(self.lib.cr_set_state(self.h, solve, ctypes.c_void_p(ptr), dev), "cr_set_state")
+
+    def step(self, nsteps=1):
+        _check(self.lib.cr_step(self.h, int(nsteps)), "cr_step")
+
+    def sync(self):
+        _check(self.lib.cr_sync(self.h), "cr_sync")
+
+    def get_state(self, out=None, solve=0, check=True):
+        M, nodes = self.state_size(solve)
+        mesh = self.meshes[solve]
+        if out is None:
+            from . import inputs
+            out = np.empty((M, inputs.num_elems(mesh), inputs.nodes_per_elem(mesh)))
+        ptr, dev = _ptr_and_location(out)
+        rc = self.lib.cr_get_state(self.h, solve, ctypes.c_void_p(ptr), dev)
+        if check:
+            _check(rc, "cr_get_state")
+        return out
+
+    def info(self, solve=0, totals=False):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        steps = ctypes.c_longlong()
+        M, _ = self.state_size(solve)
+        tot = np.zeros(M + 2) if totals else None
+        rc = self.lib.cr_get_info(self.h, solve, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(steps),
+                                  tot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if totals else None)
+        out = {"t": t.value, "dt": dt.value, "steps": steps.value, "status": rc}
+        if totals:
+            out["totals"] = tot
+        return out
+
+    def time_kernels(self, nsteps, flush=None):
+        """Mean per-launch durations (ms) of the volume and face/update kernels
+        over nsteps further steps, each kernel between CUDA events on the
+        solver's stream; `flush` (a torch CUDA tensor) is overwritten before
+        every step to evict the L2."""
+        ms = (ctypes.c_double * 2)()
+        fp = ctypes.c_void_p(flush.data_ptr()) if flush is not None else None
+        nb = flush.numel() * flush.element_size() if flush is not None else 0
+        _check(self.lib.cr_time_kernels(self.h, int(nsteps), fp, nb, ms), "cr_time_kernels")
+        return ms[0], ms[1]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _current_torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0

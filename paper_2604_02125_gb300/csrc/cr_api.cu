@@ -1,0 +1,433 @@
+// cr_api.cu -- C ABI of the cRKFR library (declared in include/cr.h).
+//
+// One solve (n_solves == 1): per step the volume kernel and the fused
+// face-flux/update kernel run on the caller's stream, replayed from CUDA graphs
+// captured at set-up (1-step and 16-step graphs).  The batched form
+// (n_solves > 1) lives in cr_batched.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cr.h"
+#include "cr_internal.h"
+#include "cr_batched.h"
+
+namespace crk {
+
+// ---------------------------------------------------------------------------
+// Reference element on [0,1]: GLL points by Newton's method on
+// (1 - x^2) P_N'(x) (whose derivative is -N(N+1) P_N by Legendre's equation)
+// from Chebyshev-Lobatto guesses; weights 1/(N(N+1) P_N(x)^2); differentiation
+// matrix by barycentric weights with the negative-sum diagonal.
+// ---------------------------------------------------------------------------
+static void legendre_pd(int N, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  for (int k = 1; k < N; ++k) {
+    double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = (N == 0) ? 1.0 : p1;
+  // P_N' = N (P_{N-1} - x P_N) / (1 - x^2) away from the end points
+  *dP = (N == 0) ? 0.0 : N * (p0 - x * p1) / (1.0 - x * x);
+}
+
+void ref_tables(int N, double* xi, double* w, double D[6][6]) {
+  const double pi = 3.14159265358979323846;
+  double x[6];
+  for (int k = 0; k <= N; ++k) {
+    double xk = -std::cos(pi * k / N);
+    if (k > 0 && k < N) {
+      for (int it = 0; it < 100; ++it) {
+        double P, dP;
+        legendre_pd(N, xk, &P, &dP);
+        double dx = (1.0 - xk * xk) * dP / (N * (N + 1.0) * P);
+        xk += dx;
+        if (std::fabs(dx) < 1e-16) break;
+      }
+    }
+    x[k] = xk;
+  }
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int k = 0; k <= N; ++k) {
+    double P, dP;
+    legendre_pd(N, x[k], &P, &dP);
+    if (k == 0) P = (N % 2 == 0) ? 1.0 : -1.0;   // P_N(-1) = (-1)^N
+    if (k == N) P = 1.0;
+    xi[k] = 0.5 * (x[k] + 1.0);
+    w[k] = 1.0 / (N * (N + 1.0) * P * P);
+  }
+  double lam[6];
+  for (int j = 0; j <= N; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k <= N; ++k)
+      if (k != j) prod *= (xi[j] - xi[k]);
+    lam[j] = 1.0 / prod;
+  }
+  for (int i = 0; i <= N; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j <= N; ++j) {
+      if (i == j) continue;
+      D[i][j] = (lam[j] / lam[i]) / (xi[i] - xi[j]);
+      diag -= D[i][j];
+    }
+    D[i][i] = diag;
+  }
+}
+
+static bool get_ops(int eq, int dim, int prec, int N, VariantOps* o) {
+  if (eq == CR_EULER) {
+    if (prec == CR_FP64) {
+      if (dim == 1) return ops_euler1_fp64(N, o);
+      if (dim == 2) return ops_euler2_fp64(N, o);
+      if (dim == 3) return ops_euler3_fp64(N, o);
+    } else {
+      if (dim == 1) return ops_euler1_fp32(N, o);
+      if (dim == 2) return ops_euler2_fp32(N, o);
+      if (dim == 3) return ops_euler3_fp32(N, o);
+    }
+  } else if (eq == CR_GLM_MHD && dim == 2) {
+    return prec == CR_FP64 ? ops_mhd2_fp64(N, o) : ops_mhd2_fp32(N, o);
+  }
+  return false;
+}
+
+int default_epb(const VariantOps& o) {
+  int epb = 256 / o.NF;
+  if (epb < 1) epb = 1;
+  const size_t cap = 160 * 1024;
+  while (epb > 1 && (size_t)epb * o.vol_bytes_per_elem > cap) --epb;
+  // prefer a whole number of warps
+  for (int e = epb; e >= 1; --e)
+    if ((e * o.NF) % 32 == 0) return e;
+  return epb;
+}
+
+}  // namespace crk
+
+using namespace crk;
+
+struct cr_ctx {
+  int n_solves = 0;
+  std::vector<cr_mesh_desc> desc;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // single-solve form
+  VariantOps ops{};
+  LaunchCtx lc{};
+  long long E = 0, NP = 0;
+  int M = 0;
+  size_t partial_blocks = 0, totals_blocks = 0;
+  bool has_state = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+  // batched form
+  BatchedCtx* batched = nullptr;
+};
+
+static int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CR_OK;
+  if (e == cudaErrorMemoryAllocation) return CR_ENOMEM;
+  if (e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice || e == cudaErrorNoDevice ||
+      e == cudaErrorInsufficientDriver)
+    return CR_ENODEV;
+  return CR_ECUDA;
+}
+
+#define CR_TRY(call)                       \
+  do {                                     \
+    cudaError_t _e = (call);               \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+static bool desc_valid(const cr_mesh_desc& d) {
+  if (d.eq != CR_EULER && d.eq != CR_GLM_MHD) return false;
+  if (d.dim < 1 || d.dim > 3) return false;
+  if (d.eq == CR_GLM_MHD && (d.dim != 2 || d.vol == CR_VOL_KEP)) return false;
+  if (d.degree_N < 1 || d.degree_N > 5) return false;
+  if (d.vol < 0 || d.vol > 2 || d.surf != CR_SURF_RUSANOV) return false;
+  if (d.prec != CR_FP64 && d.prec != CR_FP32_PAIRFLUX) return false;
+  if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || d.dt_fixed < 0.0 || !(d.c_h >= 0.0)) return false;
+  for (int k = 0; k < d.dim; ++k) {
+    if (d.cells[k] < 1) return false;
+    if (!(d.hi[k] > d.lo[k])) return false;
+  }
+  return true;
+}
+
+static void free_single(cr_ctx* c) {
+  if (c->g1) cudaGraphExecDestroy(c->g1);
+  if (c->g16) cudaGraphExecDestroy(c->g16);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->lc.u);
+  cudaFree(c->lc.rbar);
+  cudaFree(c->lc.trace);
+  cudaFree(c->lc.st);
+  cudaFree(c->lc.partials);
+  cudaFree(c->lc.totals_part);
+  c->g1 = c->g16 = nullptr;
+  c->cap_stream = nullptr;
+}
+
+static int launch_step(cr_ctx* c, cudaStream_t s) {
+  CR_TRY(c->ops.volume(c->lc, s));
+  CR_TRY(c->ops.face_update(c->lc, s));
+  return CR_OK;
+}
+
+static int capture(cr_ctx* c, int steps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  CR_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = CR_OK;
+  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(c, c->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (rc != CR_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return cuda_status(e);
+}
+
+static int init_single(cr_ctx* c) {
+  const cr_mesh_desc& d = c->desc[0];
+  if (!get_ops(d.eq, d.dim, d.prec, d.degree_N, &c->ops)) return CR_EINVAL;
+  const VariantOps& o = c->ops;
+  c->M = o.M;
+  c->NP = o.NP;
+  long long E = 1;
+  for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
+  c->E = E;
+  LaunchCtx& lc = c->lc;
+  std::memset(&lc, 0, sizeof(lc));
+  lc.ma.E = E;
+  for (int k = 0; k < 3; ++k) {
+    lc.ma.cells[k] = k < d.dim ? d.cells[k] : 1;
+    lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
+  }
+  lc.ma.cfl = d.cfl;
+  lc.ma.dt_fixed = d.dt_fixed;
+  lc.ma.gamma = d.gamma;
+  lc.ma.c_h = d.c_h;
+  lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
+  lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
+  double xi[6], w[6], D[6][6];
+  ref_tables(d.degree_N, xi, w, D);
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) {
+      lc.tb64.D[p][q] = (p <= d.degree_N && q <= d.degree_N) ? D[p][q] : 0.0;
+      lc.tb32.D[p][q] = (float)lc.tb64.D[p][q];
+    }
+  for (int p = 0; p < 6; ++p) lc.tb64.w[p] = lc.tb32.w[p] = p <= d.degree_N ? w[p] : 0.0;
+  lc.tb64.iw0 = 1.0 / w[0];
+  lc.tb64.iwN = 1.0 / w[d.degree_N];
+  lc.tb32.iw0 = (float)lc.tb64.iw0;
+  lc.tb32.iwN = (float)lc.tb64.iwN;
+  lc.epb = default_epb(o);
+  const long long nodes = E * o.NP;
+  const long long NFt = E * o.NF;
+  c->partial_blocks = (size_t)((nodes + 255) / 256);
+  c->totals_blocks = c->partial_blocks;
+  int rc = CR_OK;
+  auto al = [&](void** p, size_t bytes) {
+    if (rc != CR_OK) return;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) rc = cuda_status(e);
+  };
+  al((void**)&lc.u, sizeof(double) * (size_t)o.M * nodes);
+  al(&lc.rbar, o.real_bytes * (size_t)o.M * nodes);
+  al(&lc.trace, o.real_bytes * (size_t)o.dim * 2 * o.C * NFt);
+  al((void**)&lc.st, sizeof(DevState));
+  al((void**)&lc.partials, sizeof(double) * c->partial_blocks);
+  al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
+  if (rc != CR_OK) { free_single(c); return rc; }
+  cudaError_t e = o.set_smem((size_t)lc.epb * o.vol_bytes_per_elem);
+  if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
+  CR_TRY(cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream));
+  e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
+  rc = capture(c, 1, &c->g1);
+  if (rc == CR_OK) rc = capture(c, 16, &c->g16);
+  if (rc != CR_OK) { free_single(c); return rc; }
+  return CR_OK;
+}
+
+extern "C" {
+
+int cr_init_mesh(cr_ctx** out, const cr_mesh_desc* desc, int n_solves, void* cuda_stream) {
+  if (!out) return CR_EINVAL;
+  *out = nullptr;
+  if (!desc || n_solves < 1) return CR_EINVAL;
+  for (int k = 0; k < n_solves; ++k)
+    if (!desc_valid(desc[k])) return CR_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (prop.major != 10 || prop.minor != 3) return CR_ENODEV;   // built for sm_103a only
+  cr_ctx* c = new (std::nothrow) cr_ctx();
+  if (!c) return CR_ENOMEM;
+  c->n_solves = n_solves;
+  c->desc.assign(desc, desc + n_solves);
+  c->stream = (cudaStream_t)cuda_stream;
+  c->device = dev;
+  int rc;
+  if (n_solves == 1) {
+    rc = init_single(c);
+  } else {
+    rc = batched_init(&c->batched, c->desc.data(), n_solves, c->stream);
+  }
+  if (rc != CR_OK) { delete c; return rc; }
+  *out = c;
+  return CR_OK;
+}
+
+int cr_state_size(const cr_ctx* c, int solve, int* n_vars, long long* n_nodes) {
+  if (!c || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_state_size(c->batched, solve, n_vars, n_nodes);
+  if (n_vars) *n_vars = c->M;
+  if (n_nodes) *n_nodes = c->E * c->NP;
+  return CR_OK;
+}
+
+static int read_status(cr_ctx* c) {
+  DevState h;
+  CR_TRY(cudaMemcpyAsync(&h, c->lc.st, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CR_TRY(cudaStreamSynchronize(c->stream));
+  if (h.status & ST_TIMEOUT) return CR_ETIMEOUT;
+  if (h.status & ST_NONPHYS) return CR_ENONPHYSICAL;
+  return CR_OK;
+}
+
+int cr_set_state(cr_ctx* c, int solve, const double* u, int u_on_device) {
+  if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_set_state(c->batched, solve, u, u_on_device);
+  const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         c->stream));
+  CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
+  CR_TRY(c->ops.lambda(c->lc, c->stream));
+  int rc = read_status(c);
+  c->has_state = (rc == CR_OK);
+  return rc;
+}
+
+int cr_step(cr_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return CR_EINVAL;
+  if (c->batched) return batched_step(c->batched, nsteps);
+  if (!c->has_state) return CR_EINVAL;
+  int k = 0;
+  for (; k + 16 <= nsteps; k += 16) CR_TRY(cudaGraphLaunch(c->g16, c->stream));
+  for (; k < nsteps; ++k) CR_TRY(cudaGraphLaunch(c->g1, c->stream));
+  return CR_OK;
+}
+
+int cr_sync(cr_ctx* c) {
+  if (!c) return CR_EINVAL;
+  if (c->batched) return batched_sync(c->batched);
+  return read_status(c);
+}
+
+int cr_get_state(cr_ctx* c, int solve, double* u, int u_on_device) {
+  if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_get_state(c->batched, solve, u, u_on_device);
+  const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  CR_TRY(cudaMemcpyAsync(u, c->lc.u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         c->stream));
+  return read_status(c);
+}
+
+int cr_get_info(cr_ctx* c, int solve, double* t, double* dt, long long* steps, double* totals) {
+  if (!c || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_get_info(c->batched, solve, t, dt, steps, totals);
+  DevState h;
+  CR_TRY(cudaMemcpyAsync(&h, c->lc.st, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> part;
+  if (totals) {
+    CR_TRY(c->ops.totals(c->lc, c->stream));
+    part.resize(c->totals_blocks * (c->M + 2));
+    CR_TRY(cudaMemcpyAsync(part.data(), c->lc.totals_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                           c->stream));
+  }
+  CR_TRY(cudaStreamSynchronize(c->stream));
+  if (t) *t = h.t;
+  if (dt) *dt = h.dt;
+  if (steps) *steps = h.steps;
+  if (totals) {
+    const int K = c->M + 2;
+    for (int k = 0; k < K; ++k) totals[k] = 0.0;
+    for (size_t b = 0; b < c->totals_blocks; ++b)
+      for (int k = 0; k < K; ++k) totals[k] += part[b * K + k];
+  }
+  if (h.status & ST_TIMEOUT) return CR_ETIMEOUT;
+  if (h.status & ST_NONPHYS) return CR_ENONPHYSICAL;
+  return CR_OK;
+}
+
+int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, double* ms) {
+  if (!c || nsteps < 1 || !ms) return CR_EINVAL;
+  if (c->batched) return batched_time_kernels(c->batched, nsteps, flush_buf, flush_bytes, ms);
+  if (!c->has_state) return CR_EINVAL;
+  std::vector<cudaEvent_t> ev(4 * (size_t)nsteps, nullptr);
+  int rc = CR_OK;
+  for (auto& e : ev)
+    if (rc == CR_OK && cudaEventCreate(&e) != cudaSuccess) rc = CR_ECUDA;
+  for (int k = 0; k < nsteps && rc == CR_OK; ++k) {
+    if (flush_buf && flush_bytes && cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, c->stream) != cudaSuccess) {
+      rc = CR_ECUDA;
+      break;
+    }
+    cudaEventRecord(ev[4 * k + 0], c->stream);
+    if (c->ops.volume(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
+    cudaEventRecord(ev[4 * k + 1], c->stream);
+    cudaEventRecord(ev[4 * k + 2], c->stream);
+    if (rc == CR_OK && c->ops.face_update(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
+    cudaEventRecord(ev[4 * k + 3], c->stream);
+  }
+  if (rc == CR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CR_ECUDA;
+  double tv = 0.0, tf = 0.0;
+  for (int k = 0; k < nsteps && rc == CR_OK; ++k) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]);
+    cudaEventElapsedTime(&b, ev[4 * k + 2], ev[4 * k + 3]);
+    tv += a;
+    tf += b;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc != CR_OK) return rc;
+  ms[0] = tv / nsteps;
+  ms[1] = tf / nsteps;
+  return read_status(c);
+}
+
+int cr_destroy(cr_ctx* c) {
+  if (!c) return CR_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->batched) batched_destroy(c->batched);
+  else free_single(c);
+  delete c;
+  return CR_OK;
+}
+
+const char* cr_status_string(int s) {
+  switch (s) {
+    case CR_OK: return "ok";
+    case CR_EINVAL: return "invalid argument or mesh descriptor";
+    case CR_ENOMEM: return "device allocation failed";
+    case CR_ECUDA: return "CUDA runtime error";
+    case CR_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    case CR_ETIMEOUT: return "bounded device wait expired";
+    case CR_ENODEV: return "no usable sm_103 CUDA device";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// cr_variant.cuh -- launchers of one (system, degree, precision) variant.
+#pragma once
+#include "cr_internal.h"
+
+namespace crk {
+
+template <typename R> struct PP;
+template <> struct PP<double> {
+  static const PhysParams<double>& get(const LaunchCtx& c) { return c.pp64; }
+  static const RefTab<double>& tab(const LaunchCtx& c) { return c.tb64; }
+};
+template <> struct PP<float> {
+  static const PhysParams<float>& get(const LaunchCtx& c) { return c.pp32; }
+  static const RefTab<float>& tab(const LaunchCtx& c) { return c.tb32; }
+};
+
+template <class EQ, int N, typename R>
+struct Variant {
+  using L = VolLayout<EQ, N, R>;
+  static cudaError_t volume(const LaunchCtx& c, cudaStream_t s) {
+    const long long grid = (c.ma.E + c.epb - 1) / c.epb;
+    const int threads = c.epb * L::NF;
+    const size_t smem = (size_t)c.epb * L::bytes_per_elem();
+    k_volume<EQ, N, R><<<(unsigned)grid, threads, smem, s>>>(c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma,
+                                                             PP<R>::get(c), PP<R>::tab(c));
+    return cudaGetLastError();
+  }
+  static cudaError_t face_update(const LaunchCtx& c, cudaStream_t s) {
+    const long long total = c.ma.E * L::NP;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    k_face_update<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma,
+                                                  PP<R>::get(c), PP<R>::tab(c));
+    return cudaGetLastError();
+  }
+  static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {
+    const long long total = c.ma.E * L::NP;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    k_lambda<EQ, N><<<grid, 256, 0, s>>>(c.u, c.st, c.partials, c.ma);
+    return cudaGetLastError();
+  }
+  static cudaError_t totals(const LaunchCtx& c, cudaStream_t s) {
+    const long long total = c.ma.E * L::NP;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    k_totals<EQ, N><<<grid, 256, 0, s>>>(c.u, c.totals_part, c.ma, c.tb64);
+    return cudaGetLastError();
+  }
+  static cudaError_t set_smem(size_t bytes) {
+    return cudaFuncSetAttribute(k_volume<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  static void fill(VariantOps* o) {
+    o->M = EQ::M;
+    o->NP = L::NP;
+    o->NF = L::NF;
+    o->C = trace_comps<EQ>();
+    o->dim = EQ::DIM;
+    o->vol_bytes_per_elem = L::bytes_per_elem();
+    o->real_bytes = sizeof(R);
+    o->volume = &volume;
+    o->face_update = &face_update;
+    o->lambda = &lambda;
+    o->totals = &totals;
+    o->set_smem = &set_smem;
+  }
+};
+
+template <class EQ, typename R>
+bool fill_ops(int N, VariantOps* o) {
+  switch (N) {
+    case 1: Variant<EQ, 1, R>::fill(o); return true;
+    case 2: Variant<EQ, 2, R>::fill(o); return true;
+    case 3: Variant<EQ, 3, R>::fill(o); return true;
+    case 4: Variant<EQ, 4, R>::fill(o); return true;
+    case 5: Variant<EQ, 5, R>::fill(o); return true;
+  }
+  return false;
+}
+
+}  // namespace crk

@@ -1,0 +1,502 @@
+// crkfr_kernels.cuh -- the three kernels of one cRKFR step on sm_103a.
+//
+//  k_volume       element-local cRK stages (eq. crkfr.inner) with the
+//                 flux-differencing local residual (Sec. 3, eqs.
+//                 entropy.cons.flux.dev, entropy.cons.noncons.dev), the
+//                 b-weighted volume residual of the final update (Sec. 3,
+//                 time-averaged flux differencing), and the face traces of the
+//                 time averages U, F (eq. disc.avg.flux), F^nc (Sec. 2.3) and
+//                 of lambda(u^n).  One CTA holds `epb` elements in shared
+//                 memory; one thread per line (N+1 nodes along a direction).
+//  k_face_update  the single inter-element step: per face node one
+//                 time-averaged Rusanov flux (eq. numflux.cons) and the
+//                 reduced-communication non-conservative flux B(u^{n,+-})
+//                 g^avg(U) (Sec. 2.3), applied through the g2 correction
+//                 derivatives g_R'(1) = 1/w_N, g_L'(0) = -1/w_0 (GLL + g2) in
+//                 the FP64 update (eq. crkfr.non.cons.final); then the CFL
+//                 reduction for the next dt and the physicality flag.
+//  k_lambda       CFL reduction of a state (first step after set_state).
+//  k_totals       FP64 quadrature-weighted totals (diagnostics).
+//
+// Layouts in HBM:
+//   u     [M][E][NP] FP64        state, updated in place by k_face_update
+//   rbar  [M][E][NP] R           sum_i b_i R(u^(i))
+//   trace [DIM][2][C][E][NF] R   face data; side 0 = xi_d = 0 face, side 1 = xi_d = 1;
+//         components: U (M), F^d (M), lambda_d(u^n) (1)
+//         [+ GLM-MHD: F^nc,d (M), u^n (M)]
+#pragma once
+#include "crkfr_physics.cuh"
+
+namespace crk {
+
+struct MeshArgs {
+  long long E;
+  int cells[3];
+  double inv_dx[3];
+  double cfl, dt_fixed;
+  double gamma, c_h;
+};
+
+template <typename R>
+struct RefTab {
+  R D[6][6];       // D_pq = l_q'(xi_p) on [0,1]
+  R iw0, iwN;      // 1/w_0, 1/w_N
+  double w[6];     // quadrature weights (FP64, diagnostics)
+};
+
+struct DevState {
+  double lam_max;      // max over nodes of sum_d lambda_d / dx_d of the current state
+  double dt;           // dt of the step in flight (written by k_volume)
+  double t;
+  long long steps;
+  unsigned status;     // bit 0: non-physical state, bit 1: barrier timeout
+  unsigned counter;    // last-block ticket of the reductions
+};
+
+constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
+
+template <class EQ>
+__host__ __device__ constexpr int trace_comps() { return EQ::NC ? 4 * EQ::M + 1 : 2 * EQ::M + 1; }
+
+template <class EQ, int N, typename R>
+struct VolLayout {
+  static constexpr int DIM = EQ::DIM, M = EQ::M, P = EQ::P, n = N + 1;
+  static constexpr int NP = ipow(n, DIM), NF = NP / n, S = rk_stages(N);
+  static constexpr int O_U0 = 0;
+  static constexpr int O_Q = O_U0 + M * NP;
+  static constexpr int O_RS = O_Q + P * NP;
+  static constexpr int O_UB = O_RS + S * M * NP;
+  static constexpr int O_FB = O_UB + M * NP;
+  static constexpr int O_FN = O_FB + DIM * M * NP;
+  static constexpr int O_LAM = O_FN + (EQ::NC ? DIM * M * NP : 0);
+  static constexpr int SZ = O_LAM + DIM * NP;    // elements of R per mesh element
+  static constexpr size_t bytes_per_elem() { return sizeof(R) * (size_t)SZ; }
+};
+
+// node index of the first node of line l in direction d, and its stride
+template <int n>
+__device__ __forceinline__ int line_base(int l, int stride) { return (l % stride) + (l / stride) * stride * n; }
+
+__device__ __forceinline__ long long neighbour(long long e, int d, int off, const int* cells, int dim) {
+  long long c[3] = {0, 0, 0};
+  long long r = e;
+  for (int k = 0; k < dim; ++k) { c[k] = r % cells[k]; r /= cells[k]; }
+  c[d] = (c[d] + off + cells[d]) % cells[d];
+  long long id = 0, mul = 1;
+  for (int k = 0; k < dim; ++k) { id += c[k] * mul; mul *= cells[k]; }
+  return id;
+}
+
+// ---------------------------------------------------------------------------
+// Volume kernel
+// ---------------------------------------------------------------------------
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_volume(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+         DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+  using L = VolLayout<EQ, N, R>;
+  constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
+  constexpr int C = trace_comps<EQ>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sm = reinterpret_cast<R*>(smem_raw);
+
+  const int NT = blockDim.x;
+  const int epb = NT / NF;
+  const int tid = threadIdx.x;
+  const long long E = ma.E;
+  const long long e0 = (long long)blockIdx.x * epb;
+  const int nel = (int)min((long long)epb, E - e0);
+  const int el = tid / NF, l = tid % NF;
+  const bool active = el < nel;
+  R* my = sm + (size_t)el * L::SZ;
+
+  const double dt = ma.dt_fixed > 0.0 ? ma.dt_fixed : ma.cfl / st->lam_max;
+  if (blockIdx.x == 0 && tid == 0) st->dt = dt;
+  const R dtR = (R)dt;
+
+  // u^n -> shared memory (coalesced over [v][e0..e0+nel)[p])
+  for (int idx = tid; idx < M * nel * NP; idx += NT) {
+    int v = idx / (nel * NP), r = idx % (nel * NP);
+    int ee = r / NP, p = r % NP;
+    sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = (R)u[((size_t)v * E + e0) * NP + r];
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    // ---- node phase: stage state u^(i), pair data, time-average face sums
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const int p = l * n + k;
+        R uu[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          R acc = R(0);
+#pragma unroll
+          for (int j = 0; j < i; ++j)
+            if (rk_a(N, i, j) != 0.0) acc += R(rk_a(N, i, j)) * my[L::O_RS + (j * M + v) * NP + p];
+          uu[v] = my[L::O_U0 + v * NP + p] - dtR * acc;
+        }
+        R q[P];
+        EQ::pair_data(uu, q, pp);
+#pragma unroll
+        for (int c = 0; c < P; ++c) my[L::O_Q + c * NP + p] = q[c];
+#pragma unroll
+        for (int v = 0; v < M; ++v) my[L::O_RS + (i * M + v) * NP + p] = R(0);
+        // which faces this node lies on
+        int rem = p;
+        bool onface = false;
+        int cd[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) { cd[d] = rem % n; rem /= n; onface = onface || cd[d] == 0 || cd[d] == N; }
+        if (i == 0) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            if (cd[d] == 0 || cd[d] == N) my[L::O_LAM + d * NP + p] = EQ::wave_speed(d, q, pp);
+        }
+        const double bi = rk_b(N, i);
+        if (bi != 0.0 && onface) {
+          const R b = R(bi);
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            R* ub = &my[L::O_UB + v * NP + p];
+            *ub = (i == 0 ? R(0) : *ub) + b * uu[v];
+          }
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            if (cd[d] == 0 || cd[d] == N) {
+              R f[M];
+              EQ::flux(d, q, f, pp);
+#pragma unroll
+              for (int v = 0; v < M; ++v) {
+                R* fb = &my[L::O_FB + (d * M + v) * NP + p];
+                *fb = (i == 0 ? R(0) : *fb) + b * f[v];
+              }
+              if constexpr (EQ::NC) {
+                R g[2], nc[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) nc[v] = R(0);
+                EQ::ncg(d, q, g);
+                EQ::nc_apply(d, q, g, nc);
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                  R* fn = &my[L::O_FN + (d * M + v) * NP + p];
+                  *fn = (i == 0 ? R(0) : *fn) + b * nc[v];
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- line phase: flux differencing along each direction
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      if (active) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int stride = ipow(n, d);
+        const int base = line_base<n>(l, stride);
+        R q[n][P];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int c = 0; c < P; ++c) q[k][c] = my[L::O_Q + c * NP + base + k * stride];
+        R acc[n][M];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[k][v] = R(0);
+        // D_pp f(u_p): non-zero only at the two end points of a GLL line
+        {
+          R f[M];
+          EQ::flux(d, q[0], f, pp);
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[0][v] += R(2) * tb.D[0][0] * f[v];
+          EQ::flux(d, q[N], f, pp);
+#pragma unroll
+          for (int v = 0; v < M; ++v) acc[N][v] += R(2) * tb.D[N][N] * f[v];
+        }
+        // every pair once: f_S is symmetric
+#pragma unroll
+        for (int a = 0; a < n; ++a)
+#pragma unroll
+          for (int b = a + 1; b < n; ++b) {
+            R f[M];
+            EQ::two_point(d, q[a], q[b], f, pp);
+            const R dab = R(2) * tb.D[a][b], dba = R(2) * tb.D[b][a];
+#pragma unroll
+            for (int v = 0; v < M; ++v) { acc[a][v] += dab * f[v]; acc[b][v] += dba * f[v]; }
+          }
+        if constexpr (EQ::NC) {
+          // sum_q D_pq B(u_p) g(u_q) = B(u_p) (D g)_p (no factor 2)
+#pragma unroll
+          for (int a = 0; a < n; ++a) {
+            R dg[2] = {R(0), R(0)};
+#pragma unroll
+            for (int b = 0; b < n; ++b) {
+              R g[2];
+              EQ::ncg(d, q[b], g);
+              dg[0] += tb.D[a][b] * g[0];
+              dg[1] += tb.D[a][b] * g[1];
+            }
+            EQ::nc_apply(d, q[a], dg, acc[a]);
+          }
+        }
+        const R idx_d = (R)ma.inv_dx[d];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < M; ++v) my[L::O_RS + (i * M + v) * NP + base + k * stride] += acc[k][v] * idx_d;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- outputs: Rbar = sum_i b_i R_i (coalesced over [v][elements][p])
+  for (int idx = tid; idx < M * nel * NP; idx += NT) {
+    int v = idx / (nel * NP), r = idx % (nel * NP);
+    int ee = r / NP, p = r % NP;
+    const R* mm = sm + (size_t)ee * L::SZ;
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      if (rk_b(N, i) != 0.0) s += R(rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
+    rbar[((size_t)v * E + e0) * NP + r] = s;
+  }
+  // face traces
+  const int per_comp = nel * NF;
+  for (int idx = tid; idx < DIM * 2 * C * per_comp; idx += NT) {
+    int f = idx % NF;
+    int r = idx / NF;
+    int ee = r % nel;
+    r /= nel;
+    int c = r % C;
+    r /= C;
+    int side = r % 2;
+    int d = r / 2;
+    const int stride = ipow(n, d);
+    const int p = line_base<n>(f, stride) + side * N * stride;
+    const R* mm = sm + (size_t)ee * L::SZ;
+    R val;
+    if (c < M) val = mm[L::O_UB + c * NP + p];
+    else if (c < 2 * M) val = mm[L::O_FB + (d * M + (c - M)) * NP + p];
+    else if (c == 2 * M) val = mm[L::O_LAM + d * NP + p];
+    else if (c < 3 * M + 1) val = mm[L::O_FN + (d * M + (c - 2 * M - 1)) * NP + p];
+    else val = mm[L::O_U0 + (c - 3 * M - 1) * NP + p];
+    trace[((((size_t)(d * 2 + side) * C + c) * E) + e0 + ee) * NF + f] = val;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-wide max / or, then the last block finalises the grid reduction
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finalize_lambda(double lam, bool bad, DevState* st, double* partials,
+                                                bool advance_time) {
+  __shared__ double s_max[32];
+  __shared__ bool s_last;
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  unsigned anybad = __ballot_sync(0xffffffffu, bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_max[w] = lam;
+    if (anybad) atomicOr(&st->status, ST_NONPHYS);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_max[k]);
+    partials[blockIdx.x] = m;
+    __threadfence();
+    unsigned ticket = atomicAdd(&st->counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double m = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) m = fmax(m, __ldcg(&partials[k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_max[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mm = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, s_max[k]);
+      st->lam_max = mm;
+      if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
+      if (advance_time) { st->t += st->dt; st->steps += 1; }
+      st->counter = 0u;
+    }
+  }
+}
+
+template <class EQ>
+__device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs& ma, double& lam) {
+  if constexpr (EQ::NC) return EQ::physical(uu, ma.gamma, ma.c_h, lam, ma.inv_dx);
+  else return EQ::physical(uu, ma.gamma, lam, ma.inv_dx);
+}
+
+// ---------------------------------------------------------------------------
+// Face + update kernel: one thread per node
+// ---------------------------------------------------------------------------
+template <class EQ, int N, typename R>
+__device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
+                                          long long e_oth, int f, R* J, const PhysParams<R>& pp) {
+  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, C = trace_comps<EQ>();
+  const int side_oth = 1 - side_own;
+  auto at = [&](int side, long long e, int c) -> R {
+    return trace[((((size_t)(d * 2 + side) * C + c) * E) + e) * NF + f];
+  };
+  R Uo[M], Fo[M], Ux[M], Fx[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    Uo[v] = at(side_own, e_own, v);
+    Fo[v] = at(side_own, e_own, M + v);
+    Ux[v] = at(side_oth, e_oth, v);
+    Fx[v] = at(side_oth, e_oth, M + v);
+  }
+  const R lam = fmax(at(side_own, e_own, 2 * M), at(side_oth, e_oth, 2 * M));
+  // own is the '-' state when it is the xi = 1 side
+  const R sgn = side_own == 1 ? R(1) : R(-1);   // U+ - U- = sgn (Ux - Uo)
+#pragma unroll
+  for (int v = 0; v < M; ++v) J[v] = R(0.5) * (Fo[v] + Fx[v]) - R(0.5) * lam * sgn * (Ux[v] - Uo[v]) - Fo[v];
+  if constexpr (EQ::NC) {
+    // + B(u^n_own) g^avg(U) - F^nc_own
+    R un[M], q[EQ::P];
+#pragma unroll
+    for (int v = 0; v < M; ++v) un[v] = at(side_own, e_own, 3 * M + 1 + v);
+    EQ::pair_data(un, q, pp);
+    R g[2];
+    g[0] = R(0.5) * (Uo[5 + d] + Ux[5 + d]);
+    g[1] = R(0.5) * (Uo[8] + Ux[8]);
+    EQ::nc_apply(d, q, g, J);
+#pragma unroll
+    for (int v = 0; v < M; ++v) J[v] -= at(side_own, e_own, 2 * M + 1 + v);
+  }
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+              DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
+              const PhysParams<R> pp, const RefTab<R> tb) {
+  constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM);
+  const long long E = ma.E;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double lam = 0.0;
+  bool bad = false;
+  if (gid < E * NP) {
+    const long long e = gid / NP;
+    const int p = (int)(gid % NP);
+    const double dt = st->dt;
+    double uu[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      const size_t g = ((size_t)v * E + e) * NP + p;
+      uu[v] = u[g] - dt * (double)rbar[g];
+    }
+    int rem = p;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int cd = rem % n;
+      rem /= n;
+      const int stride = ipow(n, d);
+      const int f = (p % stride) + (p / (stride * n)) * stride;
+      if (cd == N) {   // face xi_d = 1: element is the '-' state; - dt J^- g_R'(1)/dx
+        const long long nb = neighbour(e, d, +1, ma.cells, DIM);
+        R J[M];
+        face_jump<EQ, N, R>(trace, E, d, 1, e, nb, f, J, pp);
+        const double s = dt * (double)tb.iwN * ma.inv_dx[d];
+#pragma unroll
+        for (int v = 0; v < M; ++v) uu[v] -= s * (double)J[v];
+      }
+      if (cd == 0) {   // face xi_d = 0: element is the '+' state; - dt J^+ g_L'(0)/dx, g_L'(0) = -1/w_0
+        const long long nb = neighbour(e, d, -1, ma.cells, DIM);
+        R J[M];
+        face_jump<EQ, N, R>(trace, E, d, 0, e, nb, f, J, pp);
+        const double s = dt * (double)tb.iw0 * ma.inv_dx[d];
+#pragma unroll
+        for (int v = 0; v < M; ++v) uu[v] += s * (double)J[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) u[((size_t)v * E + e) * NP + p] = uu[v];
+    bad = !physical_state<EQ>(uu, ma, lam);
+  }
+  finalize_lambda(lam, bad, st, partials, true);
+}
+
+// CFL reduction of the current state (used after set_state)
+template <class EQ, int N>
+__global__ void __launch_bounds__(256)
+k_lambda(const double* __restrict__ u, DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma) {
+  constexpr int M = EQ::M, NP = ipow(N + 1, EQ::DIM);
+  const long long E = ma.E;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double lam = 0.0;
+  bool bad = false;
+  if (gid < E * NP) {
+    const long long e = gid / NP;
+    const int p = (int)(gid % NP);
+    double uu[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) uu[v] = u[((size_t)v * E + e) * NP + p];
+    bad = !physical_state<EQ>(uu, ma, lam);
+  }
+  finalize_lambda(lam, bad, st, partials, false);
+}
+
+// FP64 quadrature-weighted totals: per block partial sums, fixed order
+template <class EQ, int N>
+__global__ void __launch_bounds__(256)
+k_totals(const double* __restrict__ u, double* __restrict__ part, const MeshArgs ma, const RefTab<double> tb) {
+  constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), K = M + 2;
+  const long long E = ma.E;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  if (gid < E * NP) {
+    const long long e = gid / NP;
+    const int p = (int)(gid % NP);
+    double wq = 1.0;
+    int rem = p;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) { wq *= tb.w[rem % n] / ma.inv_dx[d]; rem /= n; }
+    double uu[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) { uu[v] = u[((size_t)v * E + e) * NP + p]; acc[v] = wq * uu[v]; }
+    double rho = uu[0], ke = 0.0, p_;
+    if constexpr (EQ::NC) {
+      double vv = (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / rho;
+      ke = 0.5 * vv;
+      p_ = (ma.gamma - 1.0) * (uu[4] - ke - 0.5 * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]) - 0.5 * uu[8] * uu[8]);
+    } else {
+      double mm = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) mm += uu[1 + k] * uu[1 + k];
+      ke = 0.5 * mm / rho;
+      p_ = (ma.gamma - 1.0) * (uu[DIM + 1] - ke);
+    }
+    acc[M] = wq * ke;
+    acc[M + 1] = wq * (-rho * (log(p_) - ma.gamma * log(rho)) / (ma.gamma - 1.0));
+  }
+  __shared__ double s[K][256];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[(size_t)blockIdx.x * K + k] = s[k][0];
+}
+
+}  // namespace crk

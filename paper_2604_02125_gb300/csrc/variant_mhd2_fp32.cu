@@ -1,0 +1,5 @@
+// Instantiation of the cRKFR kernels for one (system, precision); N = 1..5.
+#include "cr_variant.cuh"
+namespace crk {
+bool ops_mhd2_fp32(int N, VariantOps* o) { return fill_ops<GlmMhd, float>(N, o); }
+}  // namespace crk
