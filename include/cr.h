@@ -42,6 +42,7 @@ extern "C" {
 #define CR_ENONPHYSICAL (-4)   /* a step produced rho <= 0, p <= 0 or a non-finite value */
 #define CR_ETIMEOUT     (-5)   /* a bounded device wait (batched grid barrier) expired  */
 #define CR_ENODEV       (-6)   /* no usable CUDA device / wrong architecture           */
+#define CR_ETOOLARGE    (-7)   /* mesh needs more scratch than cr_step_noalloc holds    */
 
 /* system (eq. flux.and.non.cons) */
 #define CR_EULER   0           /* compressible Euler, dim 1..3                         */
@@ -127,6 +128,29 @@ int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps,
  * batched form: ms[0] = one persistent step launch, ms[1] = 0).  The state
  * advances exactly as with cr_step.  Synchronises the stream. */
 int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
+
+/* One time step without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they advance a solve -- an application whose memory
+ * pool already holds the device, or a host loop that must not stall other
+ * streams (cudaMalloc/cudaFree can synchronise the device).
+ *   desc       : one mesh descriptor (as for cr_init_mesh).
+ *   u_in       : device pointer, state u^n (layout above), not modified
+ *                unless u_in == u_out.
+ *   u_out      : device pointer, receives u^{n+1}; may equal u_in.
+ *   dt_out     : device pointer receiving the dt used (FP64), or NULL.
+ *   cuda_stream: stream for all work (asynchronous; nothing is synchronised).
+ * dt follows the descriptor (CFL rule on u^n, or dt_fixed).  The scratch
+ * (residual sums, face traces, reductions, step record) lives in one static
+ * device array of CR_NOALLOC_SCRATCH_BYTES per device, held until the
+ * process exits; a mesh needing more returns CR_ETOOLARGE (roughly 80k nodes
+ * of 2D Euler in FP64).  The first call on a device looks up that array's
+ * device address, so make it before any stream capture.  Every call shares
+ * the array: calls that overlap on the GPU race.  Physicality is not
+ * reported; use the regular entry points for status. */
+#define CR_NOALLOC_SCRATCH_BYTES (8u << 20)
+int cr_step_noalloc(const cr_mesh_desc *desc, const double *u_in, double *u_out, double *dt_out,
+                    void *cuda_stream);
 
 /* Release every device buffer and graph of the context. */
 int cr_destroy(cr_ctx *ctx);

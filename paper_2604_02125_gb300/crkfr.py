@@ -13,7 +13,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcrkfr.so")
 
-CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENONPHYSICAL, CR_ETIMEOUT, CR_ENODEV = 0, -1, -2, -3, -4, -5, -6
+CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENONPHYSICAL, CR_ETIMEOUT, CR_ENODEV, CR_ETOOLARGE = \
+    0, -1, -2, -3, -4, -5, -6, -7
 EQ = {"euler": 0, "glm_mhd": 1}
 VOL = {"ec": 0, "kep": 1, "central": 2}
 SURF = {"rusanov": 0}
@@ -37,7 +38,7 @@ class MeshDesc(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
-           "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string")
+           "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc")
 
 
 def load_library(path=None):
@@ -59,6 +60,7 @@ def load_library(path=None):
     lib.cr_get_info.argtypes = [vp, ip, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp]
     lib.cr_time_kernels.argtypes = [vp, ip, vp, ctypes.c_size_t, dp]
     lib.cr_destroy.argtypes = [vp]
+    lib.cr_step_noalloc.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, vp]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -208,6 +210,27 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def step_noalloc(mesh, u_in, u_out, dt_out=None, prec="fp64", dt_fixed=0.0, stream=None):
+    """One step through cr_step_noalloc: no device memory is allocated; the
+    scratch is the library's static per-device array.  u_in, u_out (and dt_out,
+    a 1-element float64 tensor) are CUDA tensors; u_out may be u_in.  Returns
+    the C status (raises CrError on failure)."""
+    lib = load_library()
+    d = make_desc(mesh, prec, dt_fixed)
+    if stream is None:
+        stream = _current_torch_stream()
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    for t in (u_in, u_out) + ((dt_out,) if dt_out is not None else ()):
+        if not getattr(t, "is_cuda", False):
+            raise ValueError("cr_step_noalloc takes device tensors")
+    rc = lib.cr_step_noalloc(ctypes.byref(d), ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(u_out.data_ptr()),
+                             ctypes.c_void_p(dt_out.data_ptr()) if dt_out is not None else None,
+                             ctypes.c_void_p(int(stream or 0)))
+    _check(rc, "cr_step_noalloc")
+    return rc
 
 
 def _current_torch_stream():

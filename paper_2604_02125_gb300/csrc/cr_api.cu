@@ -80,7 +80,7 @@ void ref_tables(int N, double* xi, double* w, double D[6][6]) {
   }
 }
 
-static bool get_ops(int eq, int dim, int prec, int N, VariantOps* o) {
+bool get_ops(int eq, int dim, int prec, int N, VariantOps* o) {
   if (eq == CR_EULER) {
     if (prec == CR_FP64) {
       if (dim == 1) return ops_euler1_fp64(N, o);
@@ -426,6 +426,7 @@ const char* cr_status_string(int s) {
     case CR_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
     case CR_ETIMEOUT: return "bounded device wait expired";
     case CR_ENODEV: return "no usable sm_103 CUDA device";
+    case CR_ETOOLARGE: return "mesh exceeds the static scratch of cr_step_noalloc";
   }
   return "unknown status";
 }

@@ -46,4 +46,10 @@ bool ops_mhd2_fp32(int N, VariantOps* o);
 // reference-element tables on [0,1] computed on the host (Newton on P_N', barycentric D)
 void ref_tables(int N, double* xi, double* w, double D[6][6]);
 
+// launchers of a (system, dim, precision, degree) variant; false if none
+bool get_ops(int eq, int dim, int prec, int N, VariantOps* o);
+
+// elements per CTA of the volume kernel used by every context of a variant
+int default_epb(const VariantOps& o);
+
 }  // namespace crk
