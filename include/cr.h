@@ -129,6 +129,13 @@ int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps,
  * advances exactly as with cr_step.  Synchronises the stream. */
 int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
 
+/* Measurement: throughput of one unit on the current device, measured with
+ * CUDA events (best of 3 after a warm-up): kind 0 FP32 FMA, 1 FP64 FMA,
+ * 2 MUFU reciprocal (FP32), 3 double->float conversion, 4 integer ALU
+ * (lane-operations/s; an FMA counts once), 5 device copy (bytes/s read+write,
+ * 2 GiB allocated for the call).  Synchronises the device. */
+int cr_probe_peak(int kind, double *result);
+
 /* One time step without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while they advance a solve -- an application whose memory

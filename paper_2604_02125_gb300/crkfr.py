@@ -38,7 +38,8 @@ class MeshDesc(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
-           "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc")
+           "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
+           "cr_probe_peak")
 
 
 def load_library(path=None):
@@ -61,6 +62,7 @@ def load_library(path=None):
     lib.cr_time_kernels.argtypes = [vp, ip, vp, ctypes.c_size_t, dp]
     lib.cr_destroy.argtypes = [vp]
     lib.cr_step_noalloc.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, vp]
+    lib.cr_probe_peak.argtypes = [ip, dp]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -231,6 +233,20 @@ def step_noalloc(mesh, u_in, u_out, dt_out=None, prec="fp64", dt_fixed=0.0, stre
                              ctypes.c_void_p(int(stream or 0)))
     _check(rc, "cr_step_noalloc")
     return rc
+
+
+PROBES = {"ffma": 0, "dfma": 1, "mufu_rcp": 2, "cvt_f64_f32": 3, "int_alu": 4, "copy_bytes": 5}
+
+
+def probe_peaks(kinds=None):
+    """Measured unit throughputs of the current device (lane-ops/s; copy: bytes/s)."""
+    lib = load_library()
+    out = {}
+    for name in (kinds or PROBES):
+        r = ctypes.c_double()
+        _check(lib.cr_probe_peak(PROBES[name], ctypes.byref(r)), "cr_probe_peak")
+        out[name] = r.value
+    return out
 
 
 def _current_torch_stream():

@@ -80,21 +80,70 @@ void ref_tables(int N, double* xi, double* w, double D[6][6]) {
   }
 }
 
-bool get_ops(int eq, int dim, int prec, int N, VariantOps* o) {
-  if (eq == CR_EULER) {
-    if (prec == CR_FP64) {
-      if (dim == 1) return ops_euler1_fp64(N, o);
-      if (dim == 2) return ops_euler2_fp64(N, o);
-      if (dim == 3) return ops_euler3_fp64(N, o);
-    } else {
-      if (dim == 1) return ops_euler1_fp32(N, o);
-      if (dim == 2) return ops_euler2_fp32(N, o);
-      if (dim == 3) return ops_euler3_fp32(N, o);
-    }
-  } else if (eq == CR_GLM_MHD && dim == 2) {
-    return prec == CR_FP64 ? ops_mhd2_fp64(N, o) : ops_mhd2_fp32(N, o);
-  }
+bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o) {
+  struct Entry {
+    int eq, dim, prec, vol;
+    bool (*fn)(int, VariantOps*);
+  };
+  static const Entry table[] = {
+    {0, 1, 0, 0, &ops_euler1_fp64_ec},
+    {0, 1, 0, 1, &ops_euler1_fp64_kep},
+    {0, 1, 0, 2, &ops_euler1_fp64_central},
+    {0, 1, 1, 0, &ops_euler1_fp32_ec},
+    {0, 1, 1, 1, &ops_euler1_fp32_kep},
+    {0, 1, 1, 2, &ops_euler1_fp32_central},
+    {0, 2, 0, 0, &ops_euler2_fp64_ec},
+    {0, 2, 0, 1, &ops_euler2_fp64_kep},
+    {0, 2, 0, 2, &ops_euler2_fp64_central},
+    {0, 2, 1, 0, &ops_euler2_fp32_ec},
+    {0, 2, 1, 1, &ops_euler2_fp32_kep},
+    {0, 2, 1, 2, &ops_euler2_fp32_central},
+    {0, 3, 0, 0, &ops_euler3_fp64_ec},
+    {0, 3, 0, 1, &ops_euler3_fp64_kep},
+    {0, 3, 0, 2, &ops_euler3_fp64_central},
+    {0, 3, 1, 0, &ops_euler3_fp32_ec},
+    {0, 3, 1, 1, &ops_euler3_fp32_kep},
+    {0, 3, 1, 2, &ops_euler3_fp32_central},
+    {1, 2, 0, 0, &ops_mhd2_fp64_ec},
+    {1, 2, 0, 2, &ops_mhd2_fp64_central},
+    {1, 2, 1, 0, &ops_mhd2_fp32_ec},
+    {1, 2, 1, 2, &ops_mhd2_fp32_central},
+  };
+  for (const Entry& e : table)
+    if (e.eq == eq && e.dim == dim && e.prec == prec && e.vol == vol) return e.fn(N, o);
   return false;
+}
+
+void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
+  double xi[6], w[6], D[6][6];
+  ref_tables(N, xi, w, D);
+  std::memset(t64, 0, sizeof(*t64));
+  std::memset(t32, 0, sizeof(*t32));
+  for (int p = 0; p < 6; ++p) {
+    for (int q = 0; q < 6; ++q) {
+      t64->D[p][q] = (p <= N && q <= N) ? D[p][q] : 0.0;
+      t32->D[p][q] = (float)t64->D[p][q];
+    }
+    t64->w[p] = t32->w[p] = p <= N ? w[p] : 0.0;
+  }
+  t64->iw0 = 1.0 / w[0];
+  t64->iwN = 1.0 / w[N];
+  t32->iw0 = (float)t64->iw0;
+  t32->iwN = (float)t64->iwN;
+  const int S = rk_stages(N);
+  int slot = 0;
+  for (int i = 0; i < 7; ++i) {
+    t64->b[i] = i < S ? rk_b(N, i) : 0.0;
+    t32->b[i] = (float)t64->b[i];
+    for (int j = 0; j < 7; ++j) {
+      t64->a[i][j] = (i < S && j < i) ? rk_a(N, i, j) : 0.0;
+      t32->a[i][j] = (float)t64->a[i][j];
+    }
+    // a residual is kept in a slot if a stage beyond the next one uses it
+    bool saved = false;
+    for (int k = i + 2; k < S; ++k) saved = saved || rk_a(N, k, i) != 0.0;
+    t64->slot[i] = t32->slot[i] = saved ? (signed char)slot++ : (signed char)-1;
+  }
 }
 
 int default_epb(const VariantOps& o) {
@@ -146,6 +195,10 @@ static int cuda_status(cudaError_t e) {
   } while (0)
 
 static bool desc_valid(const cr_mesh_desc& d) {
+  // node indices are 32-bit: at most 2^31 - 1 nodes per solve
+  long long nodes = 1;
+  for (int k = 0; k < d.dim && k < 3; ++k) nodes *= (long long)(d.cells[k] > 0 ? d.cells[k] : 1) * (d.degree_N + 1);
+  if (nodes >= (1LL << 31)) return false;
   if (d.eq != CR_EULER && d.eq != CR_GLM_MHD) return false;
   if (d.dim < 1 || d.dim > 3) return false;
   if (d.eq == CR_GLM_MHD && (d.dim != 2 || d.vol == CR_VOL_KEP)) return false;
@@ -195,7 +248,7 @@ static int capture(cr_ctx* c, int steps, cudaGraphExec_t* out) {
 
 static int init_single(cr_ctx* c) {
   const cr_mesh_desc& d = c->desc[0];
-  if (!get_ops(d.eq, d.dim, d.prec, d.degree_N, &c->ops)) return CR_EINVAL;
+  if (!get_ops(d.eq, d.dim, d.prec, d.vol, d.degree_N, &c->ops)) return CR_EINVAL;
   const VariantOps& o = c->ops;
   c->M = o.M;
   c->NP = o.NP;
@@ -207,6 +260,7 @@ static int init_single(cr_ctx* c) {
   lc.ma.E = E;
   for (int k = 0; k < 3; ++k) {
     lc.ma.cells[k] = k < d.dim ? d.cells[k] : 1;
+    lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
     lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
   }
   lc.ma.cfl = d.cfl;
@@ -215,18 +269,7 @@ static int init_single(cr_ctx* c) {
   lc.ma.c_h = d.c_h;
   lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
-  double xi[6], w[6], D[6][6];
-  ref_tables(d.degree_N, xi, w, D);
-  for (int p = 0; p < 6; ++p)
-    for (int q = 0; q < 6; ++q) {
-      lc.tb64.D[p][q] = (p <= d.degree_N && q <= d.degree_N) ? D[p][q] : 0.0;
-      lc.tb32.D[p][q] = (float)lc.tb64.D[p][q];
-    }
-  for (int p = 0; p < 6; ++p) lc.tb64.w[p] = lc.tb32.w[p] = p <= d.degree_N ? w[p] : 0.0;
-  lc.tb64.iw0 = 1.0 / w[0];
-  lc.tb64.iwN = 1.0 / w[d.degree_N];
-  lc.tb32.iw0 = (float)lc.tb64.iw0;
-  lc.tb32.iwN = (float)lc.tb64.iwN;
+  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
   const long long nodes = E * o.NP;
   const long long NFt = E * o.NF;
@@ -245,7 +288,7 @@ static int init_single(cr_ctx* c) {
   al((void**)&lc.partials, sizeof(double) * c->partial_blocks);
   al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
   if (rc != CR_OK) { free_single(c); return rc; }
-  cudaError_t e = o.set_smem((size_t)lc.epb * o.vol_bytes_per_elem);
+  cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   CR_TRY(cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream));
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);

@@ -23,8 +23,10 @@ struct LaunchCtx {
 };
 
 struct VariantOps {
-  int M, NP, NF, C, dim;
-  size_t vol_bytes_per_elem;   // shared memory per element of the volume kernel
+  int M, NP, NF, C, dim;       // C: record length of a face trace (padded)
+  size_t vol_bytes_per_elem;   // shared memory per element of the tile volume kernel
+  bool lanes;                  // the lane-form volume kernel is used (32 elements per CTA)
+  size_t (*vol_smem)(int epb); // dynamic shared memory of one volume CTA
   size_t real_bytes;           // sizeof(R)
   cudaError_t (*volume)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*face_update)(const LaunchCtx&, cudaStream_t);
@@ -33,21 +35,38 @@ struct VariantOps {
   cudaError_t (*set_smem)(size_t bytes);
 };
 
-// one getter per (system, dim, precision); N = 1..5; returns false if absent
-bool ops_euler1_fp64(int N, VariantOps* o);
-bool ops_euler2_fp64(int N, VariantOps* o);
-bool ops_euler3_fp64(int N, VariantOps* o);
-bool ops_mhd2_fp64(int N, VariantOps* o);
-bool ops_euler1_fp32(int N, VariantOps* o);
-bool ops_euler2_fp32(int N, VariantOps* o);
-bool ops_euler3_fp32(int N, VariantOps* o);
-bool ops_mhd2_fp32(int N, VariantOps* o);
+// one getter per (system, dim, precision, volume flux); N = 1..5; false if absent
+bool ops_euler1_fp64_ec(int N, VariantOps* o);
+bool ops_euler1_fp64_kep(int N, VariantOps* o);
+bool ops_euler1_fp64_central(int N, VariantOps* o);
+bool ops_euler1_fp32_ec(int N, VariantOps* o);
+bool ops_euler1_fp32_kep(int N, VariantOps* o);
+bool ops_euler1_fp32_central(int N, VariantOps* o);
+bool ops_euler2_fp64_ec(int N, VariantOps* o);
+bool ops_euler2_fp64_kep(int N, VariantOps* o);
+bool ops_euler2_fp64_central(int N, VariantOps* o);
+bool ops_euler2_fp32_ec(int N, VariantOps* o);
+bool ops_euler2_fp32_kep(int N, VariantOps* o);
+bool ops_euler2_fp32_central(int N, VariantOps* o);
+bool ops_euler3_fp64_ec(int N, VariantOps* o);
+bool ops_euler3_fp64_kep(int N, VariantOps* o);
+bool ops_euler3_fp64_central(int N, VariantOps* o);
+bool ops_euler3_fp32_ec(int N, VariantOps* o);
+bool ops_euler3_fp32_kep(int N, VariantOps* o);
+bool ops_euler3_fp32_central(int N, VariantOps* o);
+bool ops_mhd2_fp64_ec(int N, VariantOps* o);
+bool ops_mhd2_fp64_central(int N, VariantOps* o);
+bool ops_mhd2_fp32_ec(int N, VariantOps* o);
+bool ops_mhd2_fp32_central(int N, VariantOps* o);
 
 // reference-element tables on [0,1] computed on the host (Newton on P_N', barycentric D)
 void ref_tables(int N, double* xi, double* w, double D[6][6]);
 
+// reference-element and tableau tables of degree N in both precisions
+void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32);
+
 // launchers of a (system, dim, precision, degree) variant; false if none
-bool get_ops(int eq, int dim, int prec, int N, VariantOps* o);
+bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o);
 
 // elements per CTA of the volume kernel used by every context of a variant
 int default_epb(const VariantOps& o);

@@ -79,7 +79,7 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   if (!desc || !u_in || !u_out || !desc_ok(*desc)) return CR_EINVAL;
   const cr_mesh_desc& d = *desc;
   VariantOps o;
-  if (!get_ops(d.eq, d.dim, d.prec, d.degree_N, &o)) return CR_EINVAL;
+  if (!get_ops(d.eq, d.dim, d.prec, d.vol, d.degree_N, &o)) return CR_EINVAL;
   long long E = 1;
   for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
   const long long nodes = E * o.NP;
@@ -110,6 +110,7 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   lc.ma.E = E;
   for (int k = 0; k < 3; ++k) {
     lc.ma.cells[k] = k < d.dim ? d.cells[k] : 1;
+    lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
     lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
   }
   lc.ma.cfl = d.cfl;
@@ -118,22 +119,10 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   lc.ma.c_h = d.c_h;
   lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
-  double xi[6], w[6], D[6][6];
-  ref_tables(d.degree_N, xi, w, D);
-  for (int p = 0; p < 6; ++p) {
-    for (int q = 0; q < 6; ++q) {
-      lc.tb64.D[p][q] = (p <= d.degree_N && q <= d.degree_N) ? D[p][q] : 0.0;
-      lc.tb32.D[p][q] = (float)lc.tb64.D[p][q];
-    }
-    lc.tb64.w[p] = lc.tb32.w[p] = p <= d.degree_N ? w[p] : 0.0;
-  }
-  lc.tb64.iw0 = 1.0 / w[0];
-  lc.tb64.iwN = 1.0 / w[d.degree_N];
-  lc.tb32.iw0 = (float)lc.tb64.iw0;
-  lc.tb32.iwN = (float)lc.tb64.iwN;
+  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
 
-  if ((e = o.set_smem((size_t)lc.epb * o.vol_bytes_per_elem)) != cudaSuccess) return to_status(e);
+  if ((e = o.set_smem(o.vol_smem(lc.epb))) != cudaSuccess) return to_status(e);
   if (u_out != u_in &&
       (e = cudaMemcpyAsync(u_out, u_in, sizeof(double) * (size_t)o.M * nodes, cudaMemcpyDeviceToDevice, s)) !=
           cudaSuccess)

@@ -1,0 +1,134 @@
+// cr_probe.cu -- throughput probes of the units the cRKFR kernels use.
+//
+// The measured peaks cover HBM copy and BF16 tensor throughput only; the
+// pair fluxes run on the FP32 FMA pipe and the MUFU unit, the state update on
+// the FP64 pipe (which on this GPU also executes float <-> double
+// conversions).  Each probe runs independent operation chains on every SM
+// (8 chains per thread, 256 threads per CTA, 8 CTAs per SM) and is timed with
+// CUDA events; results are lane-operations per second (HBM: bytes/s read+write).
+#include <cuda_runtime.h>
+
+#include "../../include/cr.h"
+
+namespace {
+
+constexpr int kIters = 4096;
+
+__global__ void __launch_bounds__(256) p_ffma(float* out, float a, float b) {
+  float x[8];
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3f + k;
+  for (int i = 0; i < kIters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+  float s = 0.f;
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) p_dfma(double* out, double a, double b) {
+  double x[8];
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < kIters / 16; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  double s = 0.0;
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.0) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) p_rcp(float* out) {
+  float x[8];
+  for (int k = 0; k < 8; ++k) x[k] = 1.5f + threadIdx.x * 1e-3f + k;
+  for (int i = 0; i < kIters / 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(x[k]));
+      x[k] += 1.0f;   // keeps consecutive reciprocals from folding
+    }
+  float s = 0.f;
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) p_cvt_d2f(float* out) {
+  double x[8];
+  float acc[8];
+  for (int k = 0; k < 8; ++k) { x[k] = 1.25 + threadIdx.x * 1e-3 + k; acc[k] = 0.f; }
+  for (int i = 0; i < kIters / 16; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float f;
+      asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(f) : "d"(x[k]));
+      acc[k] += f;
+    }
+  float s = 0.f;
+  for (int k = 0; k < 8; ++k) s += acc[k];
+  if (s == 12345.f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) p_ialu(unsigned* out) {
+  unsigned x[8];
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 2654435761u + k;
+  for (int i = 0; i < kIters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (x[k] ^ (x[k] >> 3)) + 0x9E3779B9u;
+  unsigned s = 0;
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345u) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) p_copy(const float4* __restrict__ a, float4* __restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+}  // namespace
+
+extern "C" int cr_probe_peak(int kind, double* result) {
+  if (!result || kind < 0 || kind > 5) return CR_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CR_ENODEV;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CR_ECUDA;
+  const int blocks = sms * 8, threads = 256;
+  void* buf = nullptr;
+  size_t nvec = 0;
+  if (kind == 5) {
+    nvec = (size_t)1 << 26;   // 2 x 1 GiB of float4
+    if (cudaMalloc(&buf, 2 * nvec * sizeof(float4)) != cudaSuccess) return CR_ENOMEM;
+  } else if (cudaMalloc(&buf, 64) != cudaSuccess) {
+    return CR_ENOMEM;
+  }
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  double ops = 0.0;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(t0);
+    switch (kind) {
+      case 0: p_ffma<<<blocks, threads>>>((float*)buf, 0.999f, 1e-3f); ops = 8.0 * kIters; break;
+      case 1: p_dfma<<<blocks, threads>>>((double*)buf, 0.999, 1e-3); ops = 8.0 * (kIters / 16); break;
+      case 2: p_rcp<<<blocks, threads>>>((float*)buf); ops = 8.0 * (kIters / 4); break;
+      case 3: p_cvt_d2f<<<blocks, threads>>>((float*)buf); ops = 8.0 * (kIters / 16); break;
+      case 4: p_ialu<<<blocks, threads>>>((unsigned*)buf); ops = 8.0 * 2 * kIters; break;
+      case 5: {
+        const float4* a = (const float4*)buf;
+        float4* b = (float4*)buf + nvec;
+        p_copy<<<sms * 16, 256>>>(a, b, nvec);
+        ops = 0.0;
+        break;
+      }
+    }
+    cudaEventRecord(t1);
+    if (cudaEventSynchronize(t1) != cudaSuccess) { cudaFree(buf); return CR_ECUDA; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(buf);
+  if (cudaGetLastError() != cudaSuccess) return CR_ECUDA;
+  if (kind == 5) *result = 2.0 * nvec * sizeof(float4) / (best * 1e-3);
+  else *result = ops * (double)blocks * threads / (best * 1e-3);
+  return CR_OK;
+}

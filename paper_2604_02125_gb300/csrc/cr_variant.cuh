@@ -1,6 +1,7 @@
 // cr_variant.cuh -- launchers of one (system, degree, precision) variant.
 #pragma once
 #include "cr_internal.h"
+#include "crkfr_volume_lanes.cuh"
 
 namespace crk {
 
@@ -17,12 +18,21 @@ template <> struct PP<float> {
 template <class EQ, int N, typename R>
 struct Variant {
   using L = VolLayout<EQ, N, R>;
+  using LL = LaneLayout<EQ, N, R>;
+  static constexpr bool kLanes = LL::fits();
+  static size_t vol_smem(int epb) { return kLanes ? LL::bytes() : (size_t)epb * L::bytes_per_elem(); }
   static cudaError_t volume(const LaunchCtx& c, cudaStream_t s) {
-    const long long grid = (c.ma.E + c.epb - 1) / c.epb;
-    const int threads = c.epb * L::NF;
-    const size_t smem = (size_t)c.epb * L::bytes_per_elem();
-    k_volume<EQ, N, R><<<(unsigned)grid, threads, smem, s>>>(c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma,
-                                                             PP<R>::get(c), PP<R>::tab(c));
+    if constexpr (kLanes) {
+      const long long grid = (c.ma.E + 31) / 32;
+      k_volume_lanes<EQ, N, R><<<(unsigned)grid, LL::THREADS, LL::bytes(), s>>>(
+          c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c));
+    } else {
+      const long long grid = (c.ma.E + c.epb - 1) / c.epb;
+      const int threads = c.epb * L::NF;
+      const size_t smem = (size_t)c.epb * L::bytes_per_elem();
+      k_volume_tile<EQ, N, R><<<(unsigned)grid, threads, smem, s>>>(c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma,
+                                                                    PP<R>::get(c), PP<R>::tab(c));
+    }
     return cudaGetLastError();
   }
   static cudaError_t face_update(const LaunchCtx& c, cudaStream_t s) {
@@ -35,7 +45,7 @@ struct Variant {
   static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {
     const long long total = c.ma.E * L::NP;
     const unsigned grid = (unsigned)((total + 255) / 256);
-    k_lambda<EQ, N><<<grid, 256, 0, s>>>(c.u, c.st, c.partials, c.ma);
+    k_lambda<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.st, c.partials, c.ma);
     return cudaGetLastError();
   }
   static cudaError_t totals(const LaunchCtx& c, cudaStream_t s) {
@@ -45,15 +55,20 @@ struct Variant {
     return cudaGetLastError();
   }
   static cudaError_t set_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_volume<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if constexpr (kLanes)
+      return cudaFuncSetAttribute(k_volume_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    else
+      return cudaFuncSetAttribute(k_volume_tile<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
   static void fill(VariantOps* o) {
     o->M = EQ::M;
     o->NP = L::NP;
     o->NF = L::NF;
-    o->C = trace_comps<EQ>();
+    o->C = trace_stride<EQ, R>();
     o->dim = EQ::DIM;
     o->vol_bytes_per_elem = L::bytes_per_elem();
+    o->lanes = kLanes;
+    o->vol_smem = &vol_smem;
     o->real_bytes = sizeof(R);
     o->volume = &volume;
     o->face_update = &face_update;

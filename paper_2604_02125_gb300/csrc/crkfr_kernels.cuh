@@ -21,17 +21,40 @@
 // Layouts in HBM:
 //   u     [M][E][NP] FP64        state, updated in place by k_face_update
 //   rbar  [M][E][NP] R           sum_i b_i R(u^(i))
-//   trace [DIM][2][C][E][NF] R   face data; side 0 = xi_d = 0 face, side 1 = xi_d = 1;
-//         components: U (M), F^d (M), lambda_d(u^n) (1)
-//         [+ GLM-MHD: F^nc,d (M), u^n (M)]
+//   trace [DIM][2][NF][E][CP] R  face data; side 0 = xi_d = 0 face, side 1 = xi_d = 1;
+//         one record of CP values per face node (C used, padded to 16 bytes):
+//         U (M), F^d (M), lambda_d(u^n) (1) [+ GLM-MHD: F^nc,d (M), u^n (M)]
 #pragma once
 #include "crkfr_physics.cuh"
 
 namespace crk {
 
+// Division of n < 2^31 by an invariant d >= 1 with one wide multiply:
+// q = (n * m) >> (32 + l), l = ceil(log2 d), m = ceil(2^(32+l) / d) < 2^33.
+// With m = 2^(32+l)/d + eps, 0 <= eps < 1, the quotient is n/d + n eps / 2^(32+l)
+// and n eps / 2^(32+l) < 2^31 / 2^(32+l) <= 1/(2d), too small to change floor(n/d).
+struct FastDiv {
+  unsigned long long m;
+  unsigned shift;   // 32 + l
+  unsigned d;
+};
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.shift = 32 + l;
+  f.m = (((1ull << (32 + l)) + d - 1) / d);
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  return (unsigned)(((unsigned long long)n * f.m) >> f.shift);
+}
+
 struct MeshArgs {
-  long long E;
+  long long E;          // elements; E * (N+1)^dim < 2^31 nodes per solve
   int cells[3];
+  FastDiv cdiv[3];      // division by cells[k]
   double inv_dx[3];
   double cfl, dt_fixed;
   double gamma, c_h;
@@ -42,11 +65,14 @@ struct RefTab {
   R D[6][6];       // D_pq = l_q'(xi_p) on [0,1]
   R iw0, iwN;      // 1/w_0, 1/w_N
   double w[6];     // quadrature weights (FP64, diagnostics)
+  R a[7][7], b[7]; // Butcher tableau of the degree (same values as rk_a / rk_b)
+  signed char slot[7];   // register slot of a stage residual needed beyond the next stage, else -1
 };
 
 struct DevState {
   double lam_max;      // max over nodes of sum_d lambda_d / dx_d of the current state
-  double dt;           // dt of the step in flight (written by k_volume)
+  double dt;           // dt of the last completed step
+  double dt_next;      // dt of the next step: cfl / lam_max or dt_fixed (set by the reductions)
   double t;
   long long steps;
   unsigned status;     // bit 0: non-physical state, bit 1: barrier timeout
@@ -57,6 +83,11 @@ constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
 
 template <class EQ>
 __host__ __device__ constexpr int trace_comps() { return EQ::NC ? 4 * EQ::M + 1 : 2 * EQ::M + 1; }
+// record length in the trace array: C padded to a multiple of 16 bytes
+template <class EQ, typename R>
+__host__ __device__ constexpr int trace_stride() {
+  return (trace_comps<EQ>() + (int)(16 / sizeof(R)) - 1) / (int)(16 / sizeof(R)) * (int)(16 / sizeof(R));
+}
 
 template <class EQ, int N, typename R>
 struct VolLayout {
@@ -73,26 +104,70 @@ struct VolLayout {
   static constexpr size_t bytes_per_elem() { return sizeof(R) * (size_t)SZ; }
 };
 
+// one face record (CP values, 16-byte aligned) by vector loads / stores
+template <typename R, int CP>
+__device__ __forceinline__ void load_record(const R* __restrict__ src, R (&out)[CP]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int k = 0; k < CP / 4; ++k) {
+      float4 t = s4[k];
+      out[4 * k] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int k = 0; k < CP / 2; ++k) {
+      double2 t = s2[k];
+      out[2 * k] = t.x; out[2 * k + 1] = t.y;
+    }
+  }
+}
+template <typename R, int CP>
+__device__ __forceinline__ void store_record(R* __restrict__ dst, const R (&in)[CP]) {
+  if constexpr (sizeof(R) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int k = 0; k < CP / 4; ++k) d4[k] = make_float4(in[4 * k], in[4 * k + 1], in[4 * k + 2], in[4 * k + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int k = 0; k < CP / 2; ++k) d2[k] = make_double2(in[2 * k], in[2 * k + 1]);
+  }
+}
+
 // node index of the first node of line l in direction d, and its stride
 template <int n>
 __device__ __forceinline__ int line_base(int l, int stride) { return (l % stride) + (l / stride) * stride * n; }
 
-__device__ __forceinline__ long long neighbour(long long e, int d, int off, const int* cells, int dim) {
-  long long c[3] = {0, 0, 0};
-  long long r = e;
-  for (int k = 0; k < dim; ++k) { c[k] = r % cells[k]; r /= cells[k]; }
-  c[d] = (c[d] + off + cells[d]) % cells[d];
-  long long id = 0, mul = 1;
-  for (int k = 0; k < dim; ++k) { id += c[k] * mul; mul *= cells[k]; }
-  return id;
+// element coordinates (x fastest) of element e
+template <int DIM>
+__device__ __forceinline__ void elem_coords(unsigned e, const MeshArgs& ma, unsigned (&c)[3]) {
+  unsigned r = e;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const unsigned q = (k == DIM - 1) ? 0u : fdiv(r, ma.cdiv[k]);
+    c[k] = (k == DIM - 1) ? r : r - q * (unsigned)ma.cells[k];
+    r = q;
+  }
+}
+// periodic neighbour of element e (coordinates c) in direction d, offset +-1
+__device__ __forceinline__ unsigned neighbour_of(unsigned e, const unsigned (&c)[3], int d, int off,
+                                                 const MeshArgs& ma) {
+  unsigned stride = 1;
+  for (int k = 0; k < d; ++k) stride *= (unsigned)ma.cells[k];
+  const unsigned nd = (unsigned)ma.cells[d];
+  if (off > 0) return c[d] + 1 == nd ? e - (nd - 1) * stride : e + stride;
+  return c[d] == 0 ? e + (nd - 1) * stride : e - stride;
 }
 
 // ---------------------------------------------------------------------------
-// Volume kernel
+// Volume kernel, tile form: one CTA holds epb elements; one thread per line.
+// Used where the lane form below does not fit in shared memory.
 // ---------------------------------------------------------------------------
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
-k_volume(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
          DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
   using L = VolLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
@@ -110,16 +185,15 @@ k_volume(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ tra
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
 
-  const double dt = ma.dt_fixed > 0.0 ? ma.dt_fixed : ma.cfl / st->lam_max;
-  if (blockIdx.x == 0 && tid == 0) st->dt = dt;
-  const R dtR = (R)dt;
+  const R dtR = (R)st->dt_next;
 
   // u^n -> shared memory (coalesced over [v][e0..e0+nel)[p])
-  for (int idx = tid; idx < M * nel * NP; idx += NT) {
-    int v = idx / (nel * NP), r = idx % (nel * NP);
-    int ee = r / NP, p = r % NP;
-    sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = (R)u[((size_t)v * E + e0) * NP + r];
-  }
+#pragma unroll 1
+  for (int v = 0; v < M; ++v)
+    for (int r = tid; r < nel * NP; r += NT) {
+      const int ee = r / NP, p = r % NP;
+      sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = (R)u[((size_t)v * E + e0) * NP + r];
+    }
   __syncthreads();
 
 #pragma unroll
@@ -257,27 +331,27 @@ k_volume(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ tra
   }
 
   // ---- outputs: Rbar = sum_i b_i R_i (coalesced over [v][elements][p])
-  for (int idx = tid; idx < M * nel * NP; idx += NT) {
-    int v = idx / (nel * NP), r = idx % (nel * NP);
-    int ee = r / NP, p = r % NP;
-    const R* mm = sm + (size_t)ee * L::SZ;
-    R s = R(0);
+#pragma unroll 1
+  for (int v = 0; v < M; ++v)
+    for (int r = tid; r < nel * NP; r += NT) {
+      const int ee = r / NP, p = r % NP;
+      const R* mm = sm + (size_t)ee * L::SZ;
+      R s = R(0);
 #pragma unroll
-    for (int i = 0; i < S; ++i)
-      if (rk_b(N, i) != 0.0) s += R(rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
-    rbar[((size_t)v * E + e0) * NP + r] = s;
-  }
-  // face traces
-  const int per_comp = nel * NF;
-  for (int idx = tid; idx < DIM * 2 * C * per_comp; idx += NT) {
-    int f = idx % NF;
-    int r = idx / NF;
-    int ee = r % nel;
-    r /= nel;
-    int c = r % C;
-    r /= C;
-    int side = r % 2;
-    int d = r / 2;
+      for (int i = 0; i < S; ++i)
+        if (rk_b(N, i) != 0.0) s += R(rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
+      rbar[((size_t)v * E + e0) * NP + r] = s;
+    }
+  // face traces: per face node one record of C values (coalesced over c, f, elements)
+  constexpr int CP = trace_stride<EQ, R>();
+#pragma unroll 1
+  for (int ds = 0; ds < DIM * 2; ++ds)
+    for (int idx = tid; idx < nel * NF * C; idx += NT) {
+    const int c = idx % C;
+    const int f = (idx / C) % NF;
+    const int ee = idx / (C * NF);
+    const int side = ds & 1;
+    const int d = ds >> 1;
     const int stride = ipow(n, d);
     const int p = line_base<n>(f, stride) + side * N * stride;
     const R* mm = sm + (size_t)ee * L::SZ;
@@ -287,16 +361,17 @@ k_volume(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ tra
     else if (c == 2 * M) val = mm[L::O_LAM + d * NP + p];
     else if (c < 3 * M + 1) val = mm[L::O_FN + (d * M + (c - 2 * M - 1)) * NP + p];
     else val = mm[L::O_U0 + (c - 3 * M - 1) * NP + p];
-    trace[((((size_t)(d * 2 + side) * C + c) * E) + e0 + ee) * NF + f] = val;
+    trace[((((size_t)(d * 2 + side) * NF + f) * E) + e0 + ee) * CP + c] = val;
   }
 }
 
 // ---------------------------------------------------------------------------
 // block-wide max / or, then the last block finalises the grid reduction
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void finalize_lambda(double lam, bool bad, DevState* st, double* partials,
-                                                bool advance_time) {
-  __shared__ double s_max[32];
+template <typename T>
+__device__ __forceinline__ void finalize_lambda(T lam, bool bad, DevState* st, double* partials, bool advance_time,
+                                                double ma_cfl, double ma_dt_fixed) {
+  __shared__ T s_max[32];
   __shared__ bool s_last;
   for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
   unsigned anybad = __ballot_sync(0xffffffffu, bad);
@@ -307,9 +382,9 @@ __device__ __forceinline__ void finalize_lambda(double lam, bool bad, DevState* 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
+    T m = T(0);
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_max[k]);
-    partials[blockIdx.x] = m;
+    partials[blockIdx.x] = (double)m;
     __threadfence();
     unsigned ticket = atomicAdd(&st->counter, 1u);
     s_last = (ticket == gridDim.x - 1);
@@ -320,23 +395,44 @@ __device__ __forceinline__ void finalize_lambda(double lam, bool bad, DevState* 
     double m = 0.0;
     for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) m = fmax(m, __ldcg(&partials[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) s_max[w] = m;
+    __shared__ double s_fin[32];
+    if (lane == 0) s_fin[w] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
       double mm = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, s_max[k]);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, s_fin[k]);
+      if (advance_time) {
+        st->dt = st->dt_next;
+        st->t += st->dt;
+        st->steps += 1;
+      }
       st->lam_max = mm;
       if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
-      if (advance_time) { st->t += st->dt; st->steps += 1; }
+      st->dt_next = ma_dt_fixed > 0.0 ? ma_dt_fixed : ma_cfl / mm;
       st->counter = 0u;
     }
   }
 }
 
-template <class EQ>
+// physicality and sum_d lambda_d/dx_d of an updated state; the FP32 form
+// evaluates the wave speeds in FP32 (the dt reduction is a max, taken in FP64)
+template <class EQ, typename R = double>
 __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs& ma, double& lam) {
-  if constexpr (EQ::NC) return EQ::physical(uu, ma.gamma, ma.c_h, lam, ma.inv_dx);
-  else return EQ::physical(uu, ma.gamma, lam, ma.inv_dx);
+  if constexpr (sizeof(R) == 8) {
+    if constexpr (EQ::NC) return EQ::physical(uu, ma.gamma, ma.c_h, lam, ma.inv_dx);
+    else return EQ::physical(uu, ma.gamma, lam, ma.inv_dx);
+  } else {
+    float uf[EQ::M];
+#pragma unroll
+    for (int v = 0; v < EQ::M; ++v) uf[v] = d2f_int(uu[v]);
+    float inv_dx[3] = {(float)ma.inv_dx[0], (float)ma.inv_dx[1], (float)ma.inv_dx[2]};
+    float l = 0.f;
+    bool ok;
+    if constexpr (EQ::NC) ok = EQ::physical(uf, (float)ma.gamma, (float)ma.c_h, l, inv_dx);
+    else ok = EQ::physical(uf, (float)ma.gamma, l, inv_dx);
+    lam = (double)l;
+    return ok;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -345,36 +441,28 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
                                           long long e_oth, int f, R* J, const PhysParams<R>& pp) {
-  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, C = trace_comps<EQ>();
+  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, CP = trace_stride<EQ, R>();
   const int side_oth = 1 - side_own;
-  auto at = [&](int side, long long e, int c) -> R {
-    return trace[((((size_t)(d * 2 + side) * C + c) * E) + e) * NF + f];
-  };
-  R Uo[M], Fo[M], Ux[M], Fx[M];
+  R o[CP], x[CP];
+  load_record<R, CP>(trace + ((((size_t)(d * 2 + side_own) * NF + f) * E) + e_own) * CP, o);
+  load_record<R, CP>(trace + ((((size_t)(d * 2 + side_oth) * NF + f) * E) + e_oth) * CP, x);
+  const R lam = fmax(o[2 * M], x[2 * M]);
+  // own is the '-' state when it is the xi = 1 side: U+ - U- = sgn (Ux - Uo)
+  const R sgn = side_own == 1 ? R(1) : R(-1);
 #pragma unroll
-  for (int v = 0; v < M; ++v) {
-    Uo[v] = at(side_own, e_own, v);
-    Fo[v] = at(side_own, e_own, M + v);
-    Ux[v] = at(side_oth, e_oth, v);
-    Fx[v] = at(side_oth, e_oth, M + v);
-  }
-  const R lam = fmax(at(side_own, e_own, 2 * M), at(side_oth, e_oth, 2 * M));
-  // own is the '-' state when it is the xi = 1 side
-  const R sgn = side_own == 1 ? R(1) : R(-1);   // U+ - U- = sgn (Ux - Uo)
-#pragma unroll
-  for (int v = 0; v < M; ++v) J[v] = R(0.5) * (Fo[v] + Fx[v]) - R(0.5) * lam * sgn * (Ux[v] - Uo[v]) - Fo[v];
+  for (int v = 0; v < M; ++v) J[v] = R(0.5) * (o[M + v] + x[M + v]) - R(0.5) * lam * sgn * (x[v] - o[v]) - o[M + v];
   if constexpr (EQ::NC) {
     // + B(u^n_own) g^avg(U) - F^nc_own
     R un[M], q[EQ::P];
 #pragma unroll
-    for (int v = 0; v < M; ++v) un[v] = at(side_own, e_own, 3 * M + 1 + v);
+    for (int v = 0; v < M; ++v) un[v] = o[3 * M + 1 + v];
     EQ::pair_data(un, q, pp);
     R g[2];
-    g[0] = R(0.5) * (Uo[5 + d] + Ux[5 + d]);
-    g[1] = R(0.5) * (Uo[8] + Ux[8]);
+    g[0] = R(0.5) * (o[5 + d] + x[5 + d]);
+    g[1] = R(0.5) * (o[8] + x[8]);
     EQ::nc_apply(d, q, g, J);
 #pragma unroll
-    for (int v = 0; v < M; ++v) J[v] -= at(side_own, e_own, 2 * M + 1 + v);
+    for (int v = 0; v < M; ++v) J[v] -= o[2 * M + 1 + v];
   }
 }
 
@@ -384,20 +472,23 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
               DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
               const PhysParams<R> pp, const RefTab<R> tb) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM);
+  constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double lam = 0.0;
+  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+  R lam = R(0);
   bool bad = false;
-  if (gid < E * NP) {
-    const long long e = gid / NP;
+  if (gid < (unsigned)(E * NP)) {
+    const unsigned e = gid / NP;
     const int p = (int)(gid % NP);
-    const double dt = st->dt;
-    double uu[M];
+    unsigned ec[3] = {0, 0, 0};
+    elem_coords<DIM>(e, ma, ec);
+    const double dt = st->dt_next;
+    const R dtR = (R)dt;
+    // increment of the final update (eq. crkfr.non.cons.final) in the path's
+    // arithmetic: -dt Rbar - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx
+    R du[M];
 #pragma unroll
-    for (int v = 0; v < M; ++v) {
-      const size_t g = ((size_t)v * E + e) * NP + p;
-      uu[v] = u[g] - dt * (double)rbar[g];
-    }
+    for (int v = 0; v < M; ++v) du[v] = -dtR * rbar[((size_t)v * E + e) * NP + p];
     int rem = p;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -405,48 +496,60 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
       rem /= n;
       const int stride = ipow(n, d);
       const int f = (p % stride) + (p / (stride * n)) * stride;
-      if (cd == N) {   // face xi_d = 1: element is the '-' state; - dt J^- g_R'(1)/dx
-        const long long nb = neighbour(e, d, +1, ma.cells, DIM);
+      if (cd == N) {   // face xi_d = 1: element is the '-' state
+        const unsigned nb = neighbour_of(e, ec, d, +1, ma);
         R J[M];
         face_jump<EQ, N, R>(trace, E, d, 1, e, nb, f, J, pp);
-        const double s = dt * (double)tb.iwN * ma.inv_dx[d];
+        const R s = dtR * tb.iwN * (R)ma.inv_dx[d];
 #pragma unroll
-        for (int v = 0; v < M; ++v) uu[v] -= s * (double)J[v];
+        for (int v = 0; v < M; ++v) du[v] -= s * J[v];
       }
-      if (cd == 0) {   // face xi_d = 0: element is the '+' state; - dt J^+ g_L'(0)/dx, g_L'(0) = -1/w_0
-        const long long nb = neighbour(e, d, -1, ma.cells, DIM);
+      if (cd == 0) {   // face xi_d = 0: element is the '+' state
+        const unsigned nb = neighbour_of(e, ec, d, -1, ma);
         R J[M];
         face_jump<EQ, N, R>(trace, E, d, 0, e, nb, f, J, pp);
-        const double s = dt * (double)tb.iw0 * ma.inv_dx[d];
+        const R s = dtR * tb.iw0 * (R)ma.inv_dx[d];
 #pragma unroll
-        for (int v = 0; v < M; ++v) uu[v] += s * (double)J[v];
+        for (int v = 0; v < M; ++v) du[v] += s * J[v];
       }
     }
+    // u^{n+1} = u^n + du in FP64 (one FP64 add per variable)
+    double uu[M];
 #pragma unroll
-    for (int v = 0; v < M; ++v) u[((size_t)v * E + e) * NP + p] = uu[v];
-    bad = !physical_state<EQ>(uu, ma, lam);
+    for (int v = 0; v < M; ++v) {
+      const size_t g = ((size_t)v * E + e) * NP + p;
+      if constexpr (F32) uu[v] = u[g] + f2d_int(du[v]);
+      else uu[v] = u[g] + du[v];
+      u[g] = uu[v];
+    }
+    double l;
+    bad = !physical_state<EQ, R>(uu, ma, l);
+    lam = (R)l;
   }
-  finalize_lambda(lam, bad, st, partials, true);
+  finalize_lambda<R>(lam, bad, st, partials, true, ma.cfl, ma.dt_fixed);
 }
 
-// CFL reduction of the current state (used after set_state)
-template <class EQ, int N>
+// CFL reduction of the current state (used after set_state); wave speeds in
+// the path's arithmetic R, like the reduction inside k_face_update
+template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_lambda(const double* __restrict__ u, DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma) {
   constexpr int M = EQ::M, NP = ipow(N + 1, EQ::DIM);
   const long long E = ma.E;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double lam = 0.0;
+  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+  R lam = R(0);
   bool bad = false;
-  if (gid < E * NP) {
-    const long long e = gid / NP;
+  if (gid < (unsigned)(E * NP)) {
+    const unsigned e = gid / NP;
     const int p = (int)(gid % NP);
     double uu[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) uu[v] = u[((size_t)v * E + e) * NP + p];
-    bad = !physical_state<EQ>(uu, ma, lam);
+    double l;
+    bad = !physical_state<EQ, R>(uu, ma, l);
+    lam = (R)l;
   }
-  finalize_lambda(lam, bad, st, partials, false);
+  finalize_lambda<R>(lam, bad, st, partials, false, ma.cfl, ma.dt_fixed);
 }
 
 // FP64 quadrature-weighted totals: per block partial sums, fixed order
@@ -455,12 +558,12 @@ __global__ void __launch_bounds__(256)
 k_totals(const double* __restrict__ u, double* __restrict__ part, const MeshArgs ma, const RefTab<double> tb) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), K = M + 2;
   const long long E = ma.E;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  if (gid < E * NP) {
-    const long long e = gid / NP;
+  if (gid < (unsigned)(E * NP)) {
+    const unsigned e = gid / NP;
     const int p = (int)(gid % NP);
     double wq = 1.0;
     int rem = p;

@@ -44,8 +44,14 @@ template <typename R> struct LogMeanEps;
 template <> struct LogMeanEps<double> { static constexpr double v = 1e-4; };
 template <> struct LogMeanEps<float> { static constexpr float v = 0.05f; };
 
+// FP64: IEEE division.  FP32: the MUFU reciprocal (rcp.approx, about 1 ulp),
+// no slow-path branch.
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double plain_log(double x) { return log(x); }
 __device__ __forceinline__ float plain_log(float x) { return logf(x); }
 
@@ -69,14 +75,64 @@ __device__ __forceinline__ R inv_logmean(R a, R b) {
   return plain_log(a * fast_rcp(b)) * fast_rcp(d);
 }
 
+// Out of line so that the compiler cannot if-convert it into the common path
+// (a predicated copy would be executed by every pair).
+template <typename R>
+__device__ __noinline__ void logmean_pair_general(R a1, R b1, R a2, R b2, R& L1, R& iL2) {
+  L1 = logmean(a1, b1);
+  iL2 = inv_logmean(a2, b2);
+}
+
+// L(a1,b1) and 1/L(a2,b2) together: one branch decides for both whether the
+// series applies (the common case on resolved data), otherwise each takes its
+// own branch above.
+template <typename R>
+__device__ __forceinline__ void logmean_pair(R a1, R b1, R a2, R b2, R& L1, R& iL2) {
+  R s1 = a1 + b1, d1 = a1 - b1, s2 = a2 + b2, d2 = a2 - b2;
+  R rs1 = fast_rcp(s1), rs2 = fast_rcp(s2);
+  R f1 = d1 * rs1, f2 = d2 * rs2;
+  R u1 = f1 * f1, u2 = f2 * f2;
+  if (fmax(u1, u2) < LogMeanEps<R>::v) {
+    L1 = R(0.5) * s1 * fast_rcp(series_F(u1));
+    iL2 = R(2) * series_F(u2) * rs2;
+  } else {
+    logmean_pair_general(a1, b1, a2, b2, L1, iL2);
+  }
+}
+
+// Exact float <-> double conversions with integer instructions (the FP64 pipe
+// of this GPU is narrow and also executes the hardware conversions).  Values
+// below the normal FP32 range become signed zero; infinities, NaNs and values
+// above the FP32 range take the hardware conversion.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e < 897u) return __uint_as_float(hi & 0x80000000u);
+  if (e > 1150u) return (float)x;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | mant;
+  bits += (rest > 0x10000000u) | ((rest == 0x10000000u) & (mant & 1u));   // round to nearest even
+  return __uint_as_float(bits);
+}
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  if (e == 255u) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // ---------------------------------------------------------------------------
 // Compressible Euler in DIM dimensions: u = (rho, rho v_1..rho v_DIM, E).
 // Pair data q = (rho, v_1..v_DIM, p, aux); aux = rho/p for the EC flux,
 // e = E/rho for the KEP and central fluxes.
 // ---------------------------------------------------------------------------
-template <int DIM_>
+template <int DIM_, int VOL_ = VOL_EC>
 struct Euler {
   static constexpr int DIM = DIM_;
+  static constexpr int VOL = VOL_;
   static constexpr int M = DIM_ + 2;
   static constexpr int P = DIM_ + 3;
   static constexpr bool NC = false;
@@ -97,12 +153,13 @@ struct Euler {
     R E = u[DIM + 1];
     R p = (pp.gamma - R(1)) * (E - R(0.5) * ke);
     q[IP] = p;
-    q[IAUX] = (pp.vol == VOL_EC) ? rho / p : E * ir;
+    if constexpr (VOL == VOL_EC) q[IAUX] = rho * fast_rcp(p);
+    else q[IAUX] = E * ir;
   }
 
   template <typename R>
   __device__ __forceinline__ static R total_energy(const R* q, const PhysParams<R>& pp) {
-    if (pp.vol == VOL_EC) {
+    if constexpr (VOL == VOL_EC) {
       R ke = R(0);
 #pragma unroll
       for (int k = 0; k < DIM; ++k) ke += q[1 + k] * q[1 + k];
@@ -128,19 +185,21 @@ struct Euler {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) vavg[k] = R(0.5) * (a[1 + k] + b[1 + k]);
     R pavg = R(0.5) * (a[IP] + b[IP]);
-    if (pp.vol == VOL_EC) {
+    if constexpr (VOL == VOL_EC) {
       // Ranocha: rho^ln {{v}}, momentum f_rho {{v}} + {{p}} n, energy with
       // 1/ln-mean(rho/p) and the product p_a v_b + p_b v_a
-      R f0 = logmean(a[0], b[0]) * vavg[d];
+      R rho_ln, irp_ln;
+      logmean_pair(a[0], b[0], a[IAUX], b[IAUX], rho_ln, irp_ln);
+      R f0 = rho_ln * vavg[d];
       R vv = R(0);
 #pragma unroll
       for (int k = 0; k < DIM; ++k) vv += a[1 + k] * b[1 + k];
       f[0] = f0;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) f[1 + k] = f0 * vavg[k] + (k == d ? pavg : R(0));
-      f[DIM + 1] = f0 * (R(0.5) * vv + pp.inv_gm1 * inv_logmean(a[IAUX], b[IAUX]))
+      f[DIM + 1] = f0 * (R(0.5) * vv + pp.inv_gm1 * irp_ln)
                  + R(0.5) * (a[IP] * b[1 + d] + b[IP] * a[1 + d]);
-    } else if (pp.vol == VOL_KEP) {
+    } else if constexpr (VOL == VOL_KEP) {
       // Kennedy-Gruber: arithmetic means of rho, v, p and e = E/rho
       R ravg = R(0.5) * (a[0] + b[0]);
       R eavg = R(0.5) * (a[IAUX] + b[IAUX]);
@@ -169,19 +228,21 @@ struct Euler {
   template <typename R>
   __device__ __forceinline__ static void nc_apply(int, const R*, const R*, R*) {}
 
-  // physicality of a conserved state (rho > 0, p > 0, finite)
-  __device__ __forceinline__ static bool physical(const double* u, double gamma, double& lam_sum, const double* inv_dx) {
-    double rho = u[0];
-    double ke = 0.0;
+  // physicality of a conserved state (rho > 0, p > 0, finite) and sum_d lambda_d / dx_d
+  template <typename T>
+  __device__ __forceinline__ static bool physical(const T* u, T gamma, T& lam_sum, const T* inv_dx) {
+    T rho = u[0];
+    T ke = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) ke += u[1 + k] * u[1 + k];
-    double p = (gamma - 1.0) * (u[DIM + 1] - 0.5 * ke / rho);
-    double c = sqrt(gamma * p / rho);
-    double s = 0.0;
+    T ir = T(1) / rho;
+    T p = (gamma - T(1)) * (u[DIM + 1] - T(0.5) * ke * ir);
+    T c = sqrt(gamma * p * ir);
+    T s = T(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) s += (fabs(u[1 + k] / rho) + c) * inv_dx[k];
+    for (int k = 0; k < DIM; ++k) s += (fabs(u[1 + k] * ir) + c) * inv_dx[k];
     lam_sum = s;
-    return rho > 0.0 && p > 0.0 && isfinite(s);
+    return rho > T(0) && p > T(0) && isfinite(s);
   }
 };
 
@@ -193,8 +254,10 @@ struct Euler {
 // so g^d(u) = (B_d, psi).
 // Pair data q = (rho, v1, v2, v3, p, B1, B2, B3, psi, beta = rho/(2p), |v|^2, |B|^2, v.B).
 // ---------------------------------------------------------------------------
+template <int VOL_ = VOL_EC>
 struct GlmMhd {
   static constexpr int DIM = 2;
+  static constexpr int VOL = VOL_;
   static constexpr int M = 9;
   static constexpr int P = 13;
   static constexpr bool NC = true;
@@ -211,7 +274,7 @@ struct GlmMhd {
     R p = (pp.gamma - R(1)) * (u[4] - R(0.5) * rho * vv - R(0.5) * BB - R(0.5) * psi * psi);
     q[0] = rho; q[1] = v1; q[2] = v2; q[3] = v3; q[4] = p;
     q[5] = B1; q[6] = B2; q[7] = B3; q[8] = psi;
-    q[IBETA] = R(0.5) * rho / p;
+    q[IBETA] = R(0.5) * rho * fast_rcp(p);
     q[IV2] = vv; q[IB2] = BB; q[IVB] = v1 * B1 + v2 * B2 + v3 * B3;
   }
 
@@ -234,7 +297,7 @@ struct GlmMhd {
   // variables of S = -rho s/(gamma-1)); central flux for CR_VOL_CENTRAL.
   template <typename R>
   __device__ __forceinline__ static void two_point(int d, const R* a, const R* b, R* f, const PhysParams<R>& pp) {
-    if (pp.vol != VOL_EC) {
+    if constexpr (VOL != VOL_EC) {
       R fa[M], fb[M];
       flux(d, a, fa, pp);
       flux(d, b, fb, pp);
@@ -246,9 +309,9 @@ struct GlmMhd {
 #pragma unroll
     for (int k = 0; k < 3; ++k) { v[k] = R(0.5) * (a[1 + k] + b[1 + k]); B[k] = R(0.5) * (a[IB + k] + b[IB + k]); }
     R psi = R(0.5) * (a[IPSI] + b[IPSI]);
-    R rho_ln = logmean(a[0], b[0]);
-    R ibeta_ln = inv_logmean(a[IBETA], b[IBETA]);
-    R ptil = (a[0] + b[0]) / (R(2) * (a[IBETA] + b[IBETA]));     // {{rho}} / (2 {{beta}})
+    R rho_ln, ibeta_ln;
+    logmean_pair(a[0], b[0], a[IBETA], b[IBETA], rho_ln, ibeta_ln);
+    R ptil = (a[0] + b[0]) * fast_rcp(R(2) * (a[IBETA] + b[IBETA]));     // {{rho}} / (2 {{beta}})
     R v2avg = R(0.5) * (a[IV2] + b[IV2]);
     R B2avg = R(0.5) * (a[IB2] + b[IB2]);
     R vB2avg = R(0.5) * (a[1 + d] * a[IB2] + b[1 + d] * b[IB2]);
@@ -299,23 +362,24 @@ struct GlmMhd {
     out[8] += q[1 + d] * g1;
   }
 
-  __device__ __forceinline__ static bool physical(const double* u, double gamma, double c_h, double& lam_sum, const double* inv_dx) {
-    double rho = u[0];
-    double ir = 1.0 / rho;
-    double v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
-    double BB = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
-    double p = (gamma - 1.0) * (u[4] - 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3) - 0.5 * BB - 0.5 * u[8] * u[8]);
-    double a2 = gamma * p * ir, b2 = BB * ir, s = a2 + b2;
-    double vv[2] = {v1, v2};
-    double tot = 0.0;
+  template <typename T>
+  __device__ __forceinline__ static bool physical(const T* u, T gamma, T c_h, T& lam_sum, const T* inv_dx) {
+    T rho = u[0];
+    T ir = T(1) / rho;
+    T v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
+    T BB = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
+    T p = (gamma - T(1)) * (u[4] - T(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3) - T(0.5) * BB - T(0.5) * u[8] * u[8]);
+    T a2 = gamma * p * ir, b2 = BB * ir, s = a2 + b2;
+    T vv[2] = {v1, v2};
+    T tot = T(0);
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      double bd2 = u[5 + d] * u[5 + d] * ir;
-      double cf = sqrt(0.5 * (s + sqrt(fmax(s * s - 4.0 * a2 * bd2, 0.0))));
+      T bd2 = u[5 + d] * u[5 + d] * ir;
+      T cf = sqrt(T(0.5) * (s + sqrt(fmax(s * s - T(4) * a2 * bd2, T(0)))));
       tot += (fabs(vv[d]) + fmax(cf, c_h)) * inv_dx[d];
     }
     lam_sum = tot;
-    return rho > 0.0 && p > 0.0 && isfinite(tot);
+    return rho > T(0) && p > T(0) && isfinite(tot);
   }
 };
 

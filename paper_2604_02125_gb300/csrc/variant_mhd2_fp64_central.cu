@@ -1,0 +1,5 @@
+// Instantiation of the cRKFR kernels for one (system, precision, volume flux); N = 1..5.
+#include "cr_variant.cuh"
+namespace crk {
+bool ops_mhd2_fp64_central(int N, VariantOps* o) { return fill_ops<GlmMhd<VOL_CENTRAL>, double>(N, o); }
+}  // namespace crk
