@@ -6,6 +6,7 @@
 // (n_solves > 1) lives in cr_batched.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -263,6 +264,9 @@ static int init_single(cr_ctx* c) {
     lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
     lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
   }
+  for (int k = 0; k < 3; ++k) lc.ma.inv_dx_f[k] = (float)lc.ma.inv_dx[k];
+  lc.ma.gamma_f = (float)d.gamma;
+  lc.ma.c_h_f = (float)d.c_h;
   lc.ma.cfl = d.cfl;
   lc.ma.dt_fixed = d.dt_fixed;
   lc.ma.gamma = d.gamma;
@@ -273,7 +277,8 @@ static int init_single(cr_ctx* c) {
   lc.epb = default_epb(o);
   const long long nodes = E * o.NP;
   const long long NFt = E * o.NF;
-  c->partial_blocks = (size_t)((nodes + 255) / 256);
+  // one reduction partial per CTA of the widest grid (256 nodes or 32 elements per CTA)
+  c->partial_blocks = (size_t)std::max((nodes + 255) / 256, (E + 31) / 32);
   c->totals_blocks = c->partial_blocks;
   int rc = CR_OK;
   auto al = [&](void** p, size_t bytes) {

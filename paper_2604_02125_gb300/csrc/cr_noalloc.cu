@@ -83,7 +83,7 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   long long E = 1;
   for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
   const long long nodes = E * o.NP;
-  const size_t blocks = (size_t)((nodes + 255) / 256);
+  const size_t blocks = (size_t)(((nodes + 255) / 256) > ((E + 31) / 32) ? (nodes + 255) / 256 : (E + 31) / 32);
   // scratch layout: step record | reduction partials | rbar | face traces
   const size_t off_part = align256(sizeof(DevState));
   const size_t off_rbar = off_part + align256(sizeof(double) * blocks);
@@ -113,6 +113,9 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
     lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
     lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
   }
+  for (int k = 0; k < 3; ++k) lc.ma.inv_dx_f[k] = (float)lc.ma.inv_dx[k];
+  lc.ma.gamma_f = (float)d.gamma;
+  lc.ma.c_h_f = (float)d.c_h;
   lc.ma.cfl = d.cfl;
   lc.ma.dt_fixed = d.dt_fixed;
   lc.ma.gamma = d.gamma;

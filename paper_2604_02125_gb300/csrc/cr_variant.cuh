@@ -35,11 +35,19 @@ struct Variant {
     }
     return cudaGetLastError();
   }
+  using FL = FaceLaneLayout<EQ, N, R>;
+  static constexpr bool kFaceLanes = FL::fits();
   static cudaError_t face_update(const LaunchCtx& c, cudaStream_t s) {
-    const long long total = c.ma.E * L::NP;
-    const unsigned grid = (unsigned)((total + 255) / 256);
-    k_face_update<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma,
-                                                  PP<R>::get(c), PP<R>::tab(c));
+    if constexpr (kFaceLanes) {
+      const unsigned grid = (unsigned)((c.ma.E + 31) / 32);
+      k_face_update_lanes<EQ, N, R><<<grid, FL::THREADS, FL::bytes(), s>>>(
+          c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma, PP<R>::get(c), PP<R>::tab(c));
+    } else {
+      const long long total = c.ma.E * L::NP;
+      const unsigned grid = (unsigned)((total + 255) / 256);
+      k_face_update<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma,
+                                                    PP<R>::get(c), PP<R>::tab(c));
+    }
     return cudaGetLastError();
   }
   static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {

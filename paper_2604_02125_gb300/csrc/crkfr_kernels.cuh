@@ -58,7 +58,11 @@ struct MeshArgs {
   double inv_dx[3];
   double cfl, dt_fixed;
   double gamma, c_h;
+  float inv_dx_f[3], gamma_f, c_h_f;   // FP32 copies (no conversions on the FP64 pipe)
 };
+template <typename R> __device__ __forceinline__ R inv_dx_of(const MeshArgs& ma, int d);
+template <> __device__ __forceinline__ double inv_dx_of<double>(const MeshArgs& ma, int d) { return ma.inv_dx[d]; }
+template <> __device__ __forceinline__ float inv_dx_of<float>(const MeshArgs& ma, int d) { return ma.inv_dx_f[d]; }
 
 template <typename R>
 struct RefTab {
@@ -73,10 +77,12 @@ struct DevState {
   double lam_max;      // max over nodes of sum_d lambda_d / dx_d of the current state
   double dt;           // dt of the last completed step
   double dt_next;      // dt of the next step: cfl / lam_max or dt_fixed (set by the reductions)
+  float dt_next_f;     // the same, rounded to FP32
   double t;
   long long steps;
   unsigned status;     // bit 0: non-physical state, bit 1: barrier timeout
-  unsigned counter;    // last-block ticket of the reductions
+  unsigned counter;    // last-block / last-warp ticket of the reductions
+  unsigned long long lam_bits;   // running max (bits of a non-negative double) of the warp reduction
 };
 
 constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
@@ -185,7 +191,9 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
 
-  const R dtR = (R)st->dt_next;
+  R dtR;
+  if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
+  else dtR = st->dt_next;
 
   // u^n -> shared memory (coalesced over [v][e0..e0+nel)[p])
 #pragma unroll 1
@@ -320,7 +328,7 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
             EQ::nc_apply(d, q[a], dg, acc[a]);
           }
         }
-        const R idx_d = (R)ma.inv_dx[d];
+        const R idx_d = inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -409,15 +417,49 @@ __device__ __forceinline__ void finalize_lambda(T lam, bool bad, DevState* st, d
       st->lam_max = mm;
       if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
       st->dt_next = ma_dt_fixed > 0.0 ? ma_dt_fixed : ma_cfl / mm;
+      st->dt_next_f = (float)st->dt_next;
+      st->counter = 0u;
+    }
+  }
+}
+
+// Barrier-free CFL reduction: every warp takes its max with shuffles and
+// folds it into st->lam_bits with one 64-bit atomicMax (non-negative doubles
+// order like their bit patterns); the last warp to take a ticket sets
+// lam_max, the next dt and the time, and clears the accumulators.  Must be
+// reached by every lane of every warp of the grid.
+template <typename T>
+__device__ __forceinline__ void finalize_warps(T lam, bool bad, DevState* st, unsigned total_warps, bool advance_time,
+                                               double ma_cfl, double ma_dt_fixed) {
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (anybad) atomicOr(&st->status, ST_NONPHYS);
+    atomicMax(&st->lam_bits, (unsigned long long)__double_as_longlong((double)lam));
+    __threadfence();
+    const unsigned ticket = atomicAdd(&st->counter, 1u);
+    if (ticket == total_warps - 1) {
+      __threadfence();
+      const double mm = __longlong_as_double((long long)atomicAdd(&st->lam_bits, 0ull));
+      if (advance_time) {
+        st->dt = st->dt_next;
+        st->t += st->dt;
+        st->steps += 1;
+      }
+      st->lam_max = mm;
+      if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
+      st->dt_next = ma_dt_fixed > 0.0 ? ma_dt_fixed : ma_cfl / mm;
+      st->dt_next_f = (float)st->dt_next;
+      st->lam_bits = 0ull;
       st->counter = 0u;
     }
   }
 }
 
 // physicality and sum_d lambda_d/dx_d of an updated state; the FP32 form
-// evaluates the wave speeds in FP32 (the dt reduction is a max, taken in FP64)
-template <class EQ, typename R = double>
-__device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs& ma, double& lam) {
+// evaluates the wave speeds in FP32 (the dt reduction is a max)
+template <class EQ, typename R>
+__device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs& ma, R& lam) {
   if constexpr (sizeof(R) == 8) {
     if constexpr (EQ::NC) return EQ::physical(uu, ma.gamma, ma.c_h, lam, ma.inv_dx);
     else return EQ::physical(uu, ma.gamma, lam, ma.inv_dx);
@@ -425,13 +467,8 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
     float uf[EQ::M];
 #pragma unroll
     for (int v = 0; v < EQ::M; ++v) uf[v] = d2f_int(uu[v]);
-    float inv_dx[3] = {(float)ma.inv_dx[0], (float)ma.inv_dx[1], (float)ma.inv_dx[2]};
-    float l = 0.f;
-    bool ok;
-    if constexpr (EQ::NC) ok = EQ::physical(uf, (float)ma.gamma, (float)ma.c_h, l, inv_dx);
-    else ok = EQ::physical(uf, (float)ma.gamma, l, inv_dx);
-    lam = (double)l;
-    return ok;
+    if constexpr (EQ::NC) return EQ::physical(uf, ma.gamma_f, ma.c_h_f, lam, ma.inv_dx_f);
+    else return EQ::physical(uf, ma.gamma_f, lam, ma.inv_dx_f);
   }
 }
 
@@ -482,8 +519,9 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
     const int p = (int)(gid % NP);
     unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);
-    const double dt = st->dt_next;
-    const R dtR = (R)dt;
+    R dtR;
+    if constexpr (F32) dtR = st->dt_next_f;
+    else dtR = st->dt_next;
     // increment of the final update (eq. crkfr.non.cons.final) in the path's
     // arithmetic: -dt Rbar - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx
     R du[M];
@@ -500,7 +538,7 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
         const unsigned nb = neighbour_of(e, ec, d, +1, ma);
         R J[M];
         face_jump<EQ, N, R>(trace, E, d, 1, e, nb, f, J, pp);
-        const R s = dtR * tb.iwN * (R)ma.inv_dx[d];
+        const R s = dtR * tb.iwN * inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int v = 0; v < M; ++v) du[v] -= s * J[v];
       }
@@ -508,7 +546,7 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
         const unsigned nb = neighbour_of(e, ec, d, -1, ma);
         R J[M];
         face_jump<EQ, N, R>(trace, E, d, 0, e, nb, f, J, pp);
-        const R s = dtR * tb.iw0 * (R)ma.inv_dx[d];
+        const R s = dtR * tb.iw0 * inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int v = 0; v < M; ++v) du[v] += s * J[v];
       }
@@ -522,9 +560,7 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
       else uu[v] = u[g] + du[v];
       u[g] = uu[v];
     }
-    double l;
-    bad = !physical_state<EQ, R>(uu, ma, l);
-    lam = (R)l;
+    bad = !physical_state<EQ, R>(uu, ma, lam);
   }
   finalize_lambda<R>(lam, bad, st, partials, true, ma.cfl, ma.dt_fixed);
 }
@@ -545,9 +581,7 @@ k_lambda(const double* __restrict__ u, DevState* __restrict__ st, double* __rest
     double uu[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) uu[v] = u[((size_t)v * E + e) * NP + p];
-    double l;
-    bad = !physical_state<EQ, R>(uu, ma, l);
-    lam = (R)l;
+    bad = !physical_state<EQ, R>(uu, ma, lam);
   }
   finalize_lambda<R>(lam, bad, st, partials, false, ma.cfl, ma.dt_fixed);
 }

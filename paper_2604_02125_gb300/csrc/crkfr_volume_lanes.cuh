@@ -127,7 +127,9 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
 
-  const R dtR = (R)st->dt_next;
+  R dtR;
+  if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
+  else dtR = st->dt_next;
 
   // coordinates of this thread's x-line in the other directions (warp-uniform)
   int cy = 0, cz = 0;
@@ -246,7 +248,7 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
         }
       }
       // ---------------- x-direction flux differencing, all in registers
-      line_residual<EQ, N, R, 0>(q, ax, pp, tb, (R)ma.inv_dx[0]);
+      line_residual<EQ, N, R, 0>(q, ax, pp, tb, inv_dx_of<R>(ma, 0));
     }
     if (DIM > 1) {
       __syncthreads();   // Q of this stage visible; RY of the last stage consumed
@@ -258,7 +260,7 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < P; ++c) qy[k][c] = my[L::O_Q + c * NP + base + k * n];
-        line_residual<EQ, N, R, (DIM > 1 ? 1 : 0)>(qy, ay, pp, tb, (R)ma.inv_dx[1]);
+        line_residual<EQ, N, R, (DIM > 1 ? 1 : 0)>(qy, ay, pp, tb, inv_dx_of<R>(ma, 1));
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -274,7 +276,7 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
           for (int k = 0; k < n; ++k)
 #pragma unroll
             for (int c = 0; c < P; ++c) qz[k][c] = my[L::O_Q + c * NP + base + k * n * n];
-          line_residual<EQ, N, R, DIM - 1>(qz, az, pp, tb, (R)ma.inv_dx[DIM - 1]);
+          line_residual<EQ, N, R, DIM - 1>(qz, az, pp, tb, inv_dx_of<R>(ma, DIM - 1));
 #pragma unroll
           for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -337,6 +339,143 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
       }
     }
   }
+}
+
+}  // namespace crk
+
+namespace crk {
+
+// ---------------------------------------------------------------------------
+// Face + update kernel, lane form: 32 elements per CTA, warp = x-line index,
+// lane = element.  Every face record a warp loads (own and neighbour) is a run
+// of 32 consecutive records of the [DIM][2][NF][E][CP] trace array, and face
+// membership is uniform across the warp.  u^n (FP64) and Rbar are staged
+// through shared memory with coalesced loads; u^{n+1} leaves the same way.
+// ---------------------------------------------------------------------------
+template <class EQ, int N, typename R>
+struct FaceLaneLayout {
+  static constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1;
+  static constexpr int NP = ipow(n, DIM), NF = NP / n;
+  static constexpr int THREADS = 32 * NF;
+  static constexpr size_t bytes() { return 0; }
+  static constexpr bool fits() { return THREADS <= 1024; }
+};
+
+// n contiguous values starting at src (vector loads where the alignment allows)
+template <int n, typename T>
+__device__ __forceinline__ void load_line(const T* __restrict__ src, T (&out)[n]) {
+  if constexpr (sizeof(T) == 4 && n % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < n / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(src)[k];
+      out[4 * k] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && n % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      const double2 t = reinterpret_cast<const double2*>(src)[k];
+      out[2 * k] = t.x; out[2 * k + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < n; ++k) out[k] = src[k];
+  }
+}
+template <int n>
+__device__ __forceinline__ void store_line(double* __restrict__ dst, const double (&in)[n]) {
+  if constexpr (n % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(in[2 * k], in[2 * k + 1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < n; ++k) dst[k] = in[k];
+  }
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
+k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+                    DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
+                    const PhysParams<R> pp, const RefTab<R> tb) {
+  using L = FaceLaneLayout<EQ, N, R>;
+  constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP;
+  constexpr bool F32 = sizeof(R) == 4;
+  const int tid = threadIdx.x;
+  const int l = tid >> 5, el = tid & 31;
+  const long long E = ma.E;
+  const unsigned e0 = blockIdx.x * 32u;
+  const bool active = (long long)e0 + el < E;
+
+  R lam = R(0);
+  bool bad = false;
+  if (active) {
+    const unsigned e = e0 + el;
+    R dtR;
+    if constexpr (F32) dtR = st->dt_next_f;
+    else dtR = st->dt_next;
+    // own x-line: Rbar and u^n (N+1 contiguous values per variable)
+    R rb[M][n];
+    double un[M][n];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      const size_t g = ((size_t)v * E + e) * NP + l * n;
+      load_line<n>(rbar + g, rb[v]);
+      load_line<n>(u + g, un[v]);
+    }
+    unsigned ec[3] = {0, 0, 0};
+    elem_coords<DIM>(e, ma, ec);
+    const int cy = DIM >= 2 ? l % n : 0;
+    const int cz = DIM == 3 ? l / n : 0;
+    R du[n][M];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int v = 0; v < M; ++v) du[k][v] = -dtR * rb[v][k];
+    // x faces at the line ends (eq. crkfr.non.cons.final: - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx)
+    {
+      R Jm[M], Jp[M];
+      face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp);
+      face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp);
+      const R sR = dtR * tb.iwN * inv_dx_of<R>(ma, 0), sL = dtR * tb.iw0 * inv_dx_of<R>(ma, 0);
+#pragma unroll
+      for (int v = 0; v < M; ++v) { du[N][v] -= sR * Jm[v]; du[0][v] += sL * Jp[v]; }
+    }
+    // y / z faces: whole lines on the face (warp-uniform)
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) {
+      const int cd = d == 1 ? cy : cz;
+      if (cd == 0 || cd == N) {
+        const int side = cd == N ? 1 : 0;
+        const unsigned nb = neighbour_of(e, ec, d, side ? +1 : -1, ma);
+        const R s = side ? -(dtR * tb.iwN * inv_dx_of<R>(ma, d)) : dtR * tb.iw0 * inv_dx_of<R>(ma, d);
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          const int f = d == 1 ? (k + n * cz) : (k + n * cy);
+          R J[M];
+          face_jump<EQ, N, R>(trace, E, d, side, e, nb, f, J, pp);
+#pragma unroll
+          for (int v = 0; v < M; ++v) du[k][v] += s * J[v];
+        }
+      }
+    }
+    // u^{n+1} = u^n + du in FP64
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      double uu[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        if constexpr (F32) uu[v] = un[v][k] + f2d_int(du[k][v]);
+        else uu[v] = un[v][k] + du[k][v];
+        un[v][k] = uu[v];
+      }
+      R lk;
+      bad = bad || !physical_state<EQ, R>(uu, ma, lk);
+      lam = fmax(lam, lk);
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) store_line<n>(u + ((size_t)v * E + e) * NP + l * n, un[v]);
+  }
+  finalize_warps<R>(lam, bad, st, gridDim.x * (L::THREADS / 32), true, ma.cfl, ma.dt_fixed);
 }
 
 }  // namespace crk
