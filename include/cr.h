@@ -82,10 +82,14 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
 /* Create a context on the current CUDA device.
  *   out        : receives the context (NULL on failure).
  *   desc       : n_solves descriptors (copied).
- *   n_solves   : 1 = one mesh advanced by three kernels per step (volume, face +
- *                update, replayed as a CUDA graph); > 1 = batched form: all
- *                solves advance together in one persistent kernel per step
- *                (requires prec = CR_FP32_PAIRFLUX, eq = CR_EULER, dim = 2).
+ *   n_solves   : 1 = one mesh advanced by two kernels per step (volume, face +
+ *                update, replayed as a CUDA graph); > 1 = batched form: the
+ *                solves (meshes and degrees may differ) advance together, per
+ *                step one persistent volume kernel and one persistent face /
+ *                update kernel per degree present, all replayed from one CUDA
+ *                graph; grid sizes are autotuned before the first step.  The
+ *                batched form requires eq = CR_EULER, dim = 2 and the same
+ *                prec and vol for all solves (and the same gamma per degree).
  *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
  * The library allocates and owns all device buffers (state, stage/trace
  * scratch, reduction partials).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
@@ -158,6 +162,11 @@ int cr_probe_peak(int kind, double *result);
 #define CR_NOALLOC_SCRATCH_BYTES (8u << 20)
 int cr_step_noalloc(const cr_mesh_desc *desc, const double *u_in, double *u_out, double *dt_out,
                     void *cuda_stream);
+
+/* JSON description of the kernel configuration chosen for the context (the
+ * autotuned persistent grids of the batched form), copied into buf (len
+ * bytes, NUL-terminated).  CR_EINVAL if it does not fit. */
+int cr_tuning_info(cr_ctx *ctx, char *buf, size_t len);
 
 /* Release every device buffer and graph of the context. */
 int cr_destroy(cr_ctx *ctx);

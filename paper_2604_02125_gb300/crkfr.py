@@ -39,7 +39,7 @@ _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
            "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
-           "cr_probe_peak")
+           "cr_probe_peak", "cr_tuning_info")
 
 
 def load_library(path=None):
@@ -63,6 +63,7 @@ def load_library(path=None):
     lib.cr_destroy.argtypes = [vp]
     lib.cr_step_noalloc.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, vp]
     lib.cr_probe_peak.argtypes = [ip, dp]
+    lib.cr_tuning_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -195,6 +196,13 @@ class Solver:
         nb = flush.numel() * flush.element_size() if flush is not None else 0
         _check(self.lib.cr_time_kernels(self.h, int(nsteps), fp, nb, ms), "cr_time_kernels")
         return ms[0], ms[1]
+
+    def tuning_info(self):
+        """The kernel configuration chosen for this context (JSON)."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(self.lib.cr_tuning_info(self.h, buf, len(buf)), "cr_tuning_info")
+        return json.loads(buf.value.decode())
 
     def close(self):
         if getattr(self, "h", None):

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/cr.h"
@@ -147,6 +148,30 @@ void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
   }
 }
 
+void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* plc) {
+  LaunchCtx& lc = *plc;
+  std::memset(&lc, 0, sizeof(lc));
+  long long E = 1;
+  for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
+  lc.ma.E = E;
+  for (int k = 0; k < 3; ++k) {
+    lc.ma.cells[k] = k < d.dim ? d.cells[k] : 1;
+    lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
+    lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
+  }
+  for (int k = 0; k < 3; ++k) lc.ma.inv_dx_f[k] = (float)lc.ma.inv_dx[k];
+  lc.ma.gamma_f = (float)d.gamma;
+  lc.ma.c_h_f = (float)d.c_h;
+  lc.ma.cfl = d.cfl;
+  lc.ma.dt_fixed = d.dt_fixed;
+  lc.ma.gamma = d.gamma;
+  lc.ma.c_h = d.c_h;
+  lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
+  lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
+  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
+  lc.epb = default_epb(o);
+}
+
 int default_epb(const VariantOps& o) {
   int epb = 256 / o.NF;
   if (epb < 1) epb = 1;
@@ -257,24 +282,7 @@ static int init_single(cr_ctx* c) {
   for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
   c->E = E;
   LaunchCtx& lc = c->lc;
-  std::memset(&lc, 0, sizeof(lc));
-  lc.ma.E = E;
-  for (int k = 0; k < 3; ++k) {
-    lc.ma.cells[k] = k < d.dim ? d.cells[k] : 1;
-    lc.ma.cdiv[k] = make_fastdiv((unsigned)lc.ma.cells[k]);
-    lc.ma.inv_dx[k] = k < d.dim ? d.cells[k] / (d.hi[k] - d.lo[k]) : 0.0;
-  }
-  for (int k = 0; k < 3; ++k) lc.ma.inv_dx_f[k] = (float)lc.ma.inv_dx[k];
-  lc.ma.gamma_f = (float)d.gamma;
-  lc.ma.c_h_f = (float)d.c_h;
-  lc.ma.cfl = d.cfl;
-  lc.ma.dt_fixed = d.dt_fixed;
-  lc.ma.gamma = d.gamma;
-  lc.ma.c_h = d.c_h;
-  lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
-  lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
-  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
-  lc.epb = default_epb(o);
+  fill_launch_ctx(d, o, &lc);
   const long long nodes = E * o.NP;
   const long long NFt = E * o.NF;
   // one reduction partial per CTA of the widest grid (256 nodes or 32 elements per CTA)
@@ -463,6 +471,22 @@ int cr_destroy(cr_ctx* c) {
   else free_single(c);
   delete c;
   return CR_OK;
+}
+
+int cr_tuning_info(cr_ctx* c, char* buf, size_t len) {
+  if (!c || !buf || len == 0) return CR_EINVAL;
+  std::string info;
+  if (c->batched) {
+    info = batched_tuning(c->batched);
+  } else {
+    char tmp[256];
+    std::snprintf(tmp, sizeof(tmp), "{\"volume\": \"%s\", \"elements_per_cta\": %d, \"face\": \"%s\"}",
+                  c->ops.lanes ? "lanes" : "tile", c->ops.lanes ? 32 : c->lc.epb,
+                  c->ops.threads_face > 0 ? "lanes" : "per-node");
+    info = tmp;
+  }
+  std::snprintf(buf, len, "%s", info.c_str());
+  return info.size() < len ? CR_OK : CR_EINVAL;
 }
 
 const char* cr_status_string(int s) {

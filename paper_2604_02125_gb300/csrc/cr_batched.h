@@ -14,5 +14,6 @@ int batched_sync(BatchedCtx* b);
 int batched_get_state(BatchedCtx* b, int solve, double* u, int on_device);
 int batched_get_info(BatchedCtx* b, int solve, double* t, double* dt, long long* steps, double* totals);
 int batched_time_kernels(BatchedCtx* b, int nsteps, void* flush, size_t bytes, double* ms);
+const char* batched_tuning(const BatchedCtx* b);
 void batched_destroy(BatchedCtx* b);
 }  // namespace crk

@@ -2,7 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
-#include "crkfr_kernels.cuh"
+#include "../../include/cr.h"
+#include "crkfr_volume_lanes.cuh"
 
 namespace crk {
 
@@ -22,6 +23,18 @@ struct LaunchCtx {
   int epb;            // elements per CTA of the volume kernel
 };
 
+// One launch of a batched persistent kernel (all solves of one degree).
+struct BatchLaunch {
+  const BatchSolve* solves;
+  const BatchTile* tiles;
+  unsigned ntiles;
+  int grid;
+  PhysParams<double> pp64;
+  PhysParams<float> pp32;
+  RefTab<double> tb64;
+  RefTab<float> tb32;
+};
+
 struct VariantOps {
   int M, NP, NF, C, dim;       // C: record length of a face trace (padded)
   size_t vol_bytes_per_elem;   // shared memory per element of the tile volume kernel
@@ -33,6 +46,11 @@ struct VariantOps {
   cudaError_t (*lambda)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*totals)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*set_smem)(size_t bytes);
+  // batched persistent kernels (2D Euler only; null elsewhere)
+  cudaError_t (*vol_batched)(const BatchLaunch&, cudaStream_t);
+  cudaError_t (*face_batched)(const BatchLaunch&, cudaStream_t);
+  int (*occupancy)(int which);   // resident CTAs per SM: 0 = volume, 1 = face
+  int threads_vol, threads_face;
 };
 
 // one getter per (system, dim, precision, volume flux); N = 1..5; false if absent
@@ -70,5 +88,8 @@ bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o);
 
 // elements per CTA of the volume kernel used by every context of a variant
 int default_epb(const VariantOps& o);
+
+// mesh arguments, physics parameters and tables of one descriptor (no allocation)
+void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* lc);
 
 }  // namespace crk

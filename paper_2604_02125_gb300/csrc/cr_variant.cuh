@@ -15,6 +15,16 @@ template <> struct PP<float> {
   static const RefTab<float>& tab(const LaunchCtx& c) { return c.tb32; }
 };
 
+template <typename R> struct PPB;
+template <> struct PPB<double> {
+  static const PhysParams<double>& get(const BatchLaunch& b) { return b.pp64; }
+  static const RefTab<double>& tab(const BatchLaunch& b) { return b.tb64; }
+};
+template <> struct PPB<float> {
+  static const PhysParams<float>& get(const BatchLaunch& b) { return b.pp32; }
+  static const RefTab<float>& tab(const BatchLaunch& b) { return b.tb32; }
+};
+
 template <class EQ, int N, typename R>
 struct Variant {
   using L = VolLayout<EQ, N, R>;
@@ -68,7 +78,41 @@ struct Variant {
     else
       return cudaFuncSetAttribute(k_volume_tile<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
+  static constexpr bool kBatched = EQ::DIM == 2 && !EQ::NC && kLanes && kFaceLanes;
+  static cudaError_t vol_batched(const BatchLaunch& b, cudaStream_t s) {
+    if constexpr (kBatched) {
+      k_volume_batched<EQ, N, R><<<b.grid, LL::THREADS, LL::bytes(), s>>>(
+          b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b));
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
+  static cudaError_t face_batched(const BatchLaunch& b, cudaStream_t s) {
+    if constexpr (kBatched) {
+      k_face_batched<EQ, N, R><<<b.grid, FL::THREADS, 0, s>>>(b.solves, b.tiles, b.ntiles, PPB<R>::get(b),
+                                                              PPB<R>::tab(b));
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
+  static int occupancy(int which) {
+    int nb = 0;
+    if constexpr (kBatched) {
+      if (which == 0) {
+        cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batched<EQ, N, R>, LL::THREADS, LL::bytes());
+      } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_face_batched<EQ, N, R>, FL::THREADS, 0);
+      }
+    }
+    return nb;
+  }
   static void fill(VariantOps* o) {
+    o->vol_batched = kBatched ? &vol_batched : nullptr;
+    o->face_batched = kBatched ? &face_batched : nullptr;
+    o->occupancy = kBatched ? &occupancy : nullptr;
+    o->threads_vol = LL::THREADS;
+    o->threads_face = FL::THREADS;
     o->M = EQ::M;
     o->NP = L::NP;
     o->NF = L::NF;

@@ -107,22 +107,21 @@ struct LaneLayout {
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
 };
 
+// One tile of 32 elements starting at e0 (the CTA's whole shared memory sm).
 template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
-k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
-               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+__device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
+                                                  R* __restrict__ trace, const DevState* __restrict__ st,
+                                                  const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
+                                                  long long e0, R* sm) {
   using L = LaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
   constexpr int C = trace_comps<EQ>();
   constexpr int NS = rk_nsaved(N) > 0 ? rk_nsaved(N) : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sm = reinterpret_cast<R*>(smem_raw);
 
   const int tid = threadIdx.x;
   const int l = tid >> 5;              // line index (warp-uniform)
   const int el = tid & 31;             // element within the CTA
   const long long E = ma.E;
-  const long long e0 = (long long)blockIdx.x * 32;
   const int nel = (int)min(32LL, E - e0);
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
@@ -341,6 +340,15 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
   }
 }
 
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)blockIdx.x * 32,
+                              reinterpret_cast<R*>(smem_raw));
+}
+
 }  // namespace crk
 
 namespace crk {
@@ -392,18 +400,19 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
   }
 }
 
+// One tile of 32 elements starting at e0; total_warps = warps of all tiles of
+// this solve in the launch (for the barrier-free CFL reduction).
 template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
-k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
-                    DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
-                    const PhysParams<R> pp, const RefTab<R> tb) {
+__device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
+                                                const R* __restrict__ trace, DevState* __restrict__ st,
+                                                const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
+                                                unsigned e0, unsigned total_warps) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP;
   constexpr bool F32 = sizeof(R) == 4;
   const int tid = threadIdx.x;
   const int l = tid >> 5, el = tid & 31;
   const long long E = ma.E;
-  const unsigned e0 = blockIdx.x * 32u;
   const bool active = (long long)e0 + el < E;
 
   R lam = R(0);
@@ -475,7 +484,63 @@ k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R*
 #pragma unroll
     for (int v = 0; v < M; ++v) store_line<n>(u + ((size_t)v * E + e) * NP + l * n, un[v]);
   }
-  finalize_warps<R>(lam, bad, st, gridDim.x * (L::THREADS / 32), true, ma.cfl, ma.dt_fixed);
+  finalize_warps<R>(lam, bad, st, total_warps, true, ma.cfl, ma.dt_fixed);
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
+k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+                    DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
+                    const PhysParams<R> pp, const RefTab<R> tb) {
+  face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u,
+                            gridDim.x * (FaceLaneLayout<EQ, N, R>::THREADS / 32));
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent form: many independent solves of one degree.  Each
+// persistent CTA walks a work list of 32-element tiles spanning all solves
+// (grid-stride); the solve's mesh, buffers and step record come from a
+// device table.
+// ---------------------------------------------------------------------------
+struct BatchSolve {
+  MeshArgs ma;
+  double* u;
+  void* rbar;
+  void* trace;
+  DevState* st;
+  unsigned ntiles;     // tiles of this solve
+  unsigned pad;
+};
+struct BatchTile {
+  unsigned solve;
+  unsigned e0;
+};
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
+                 const PhysParams<R> pp, const RefTab<R> tb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const BatchTile t = tiles[it];
+    const MeshArgs ma = solves[t.solve].ma;
+    volume_lanes_tile<EQ, N, R>(solves[t.solve].u, (R*)solves[t.solve].rbar, (R*)solves[t.solve].trace,
+                                solves[t.solve].st, ma, pp, tb, (long long)t.e0, reinterpret_cast<R*>(smem_raw));
+    __syncthreads();   // shared memory is reused by the next tile
+  }
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
+k_face_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
+               const PhysParams<R> pp, const RefTab<R> tb) {
+  constexpr unsigned WPT = FaceLaneLayout<EQ, N, R>::THREADS / 32;   // warps per tile
+  for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const BatchTile t = tiles[it];
+    const MeshArgs ma = solves[t.solve].ma;
+    face_lanes_tile<EQ, N, R>(solves[t.solve].u, (const R*)solves[t.solve].rbar, (const R*)solves[t.solve].trace,
+                              solves[t.solve].st, ma, pp, tb, t.e0, solves[t.solve].ntiles * WPT);
+  }
 }
 
 }  // namespace crk

@@ -1,0 +1,104 @@
+"""Batched form: independent 2D Euler solves of uneven size and degree
+advanced together by per-degree persistent kernels (one CUDA graph).
+
+Each solve of a batch must agree with the same solve advanced alone (same
+kernels, so to round-off) and with the FP64 oracle (1e-12 per step in FP64,
+1e-5 after 100 steps for the FP32 pair-flux form); every solve keeps its own
+CFL time step.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_02125_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_02125_gb300 import build, crkfr
+    build.build()
+    return crkfr
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def small_batch(n=7, seed=5, vol="ec"):
+    specs = inputs.batched_2d_specs(n_solves=n, seed=seed, side_lo=3, side_hi=11)
+    return [inputs.batched_2d_solve(sp, vol=vol) for sp in specs]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_single_solves(cr, prec):
+    batch = small_batch()
+    meshes = [m for m, _ in batch]
+    assert len({m["N"] for m in meshes}) >= 3
+    with cr.Solver(meshes, prec=prec) as b:
+        for k, (m, U) in enumerate(batch):
+            b.set_state(U, solve=k)
+        b.step(5)
+        outs = [b.get_state(solve=k) for k in range(len(batch))]
+        infos = [b.info(solve=k) for k in range(len(batch))]
+        tun = b.tuning_info()
+    assert any(key.endswith("_volume") for key in tun)
+    for k, (m, U) in enumerate(batch):
+        with cr.Solver(m, prec=prec) as s:
+            s.set_state(U)
+            s.step(5)
+            ref = s.get_state()
+            info = s.info()
+        assert rel(outs[k], ref) <= 1e-14, (k, m["N"], rel(outs[k], ref))
+        assert infos[k]["steps"] == 5 and abs(infos[k]["t"] - info["t"]) <= 1e-15 * info["t"]
+
+
+def test_batch_fp64_vs_oracle_per_solve_dt(cr, orc):
+    batch = small_batch(n=5, seed=9)
+    meshes = [m for m, _ in batch]
+    with cr.Solver(meshes, prec="fp64") as b:
+        for k, (m, U) in enumerate(batch):
+            b.set_state(U, solve=k)
+        b.step(3)
+        for k, (m, U) in enumerate(batch):
+            ref, dts = orc.run(m, U, 3)
+            out = b.get_state(solve=k)
+            info = b.info(solve=k)
+            assert rel(out, ref) <= 1e-12, (k, rel(out, ref))
+            assert abs(info["dt"] - dts[-1]) <= 1e-13 * dts[-1]
+            assert abs(info["t"] - sum(dts)) <= 1e-13 * sum(dts)
+
+
+def test_batch_fp32_error(cr, orc):
+    batch = small_batch(n=4, seed=11)
+    meshes = [m for m, _ in batch]
+    with cr.Solver(meshes, prec="fp32") as b:
+        for k, (m, U) in enumerate(batch):
+            b.set_state(U, solve=k)
+        b.step(100)
+        for k, (m, U) in enumerate(batch):
+            ref, _ = orc.run(m, U, 100)
+            assert rel(b.get_state(solve=k), ref) <= 1e-5
+
+
+def test_batch_rejects_mixed_forms(cr):
+    batch = small_batch(n=3)
+    meshes = [dict(m) for m, _ in batch]
+    meshes[1]["vol"] = "kep"
+    with pytest.raises(cr.CrError) as ei:
+        cr.Solver(meshes, prec="fp64")
+    assert ei.value.status == cr.CR_EINVAL
+    mh, _ = inputs.mhd_vortex_2d(cells=(4, 4), N=3)
+    with pytest.raises(cr.CrError):
+        cr.Solver([mh, mh], prec="fp32")
+
+
+def test_batch_step_needs_every_state(cr):
+    batch = small_batch(n=3)
+    with cr.Solver([m for m, _ in batch], prec="fp32") as b:
+        b.set_state(batch[0][1], solve=0)
+        with pytest.raises(cr.CrError):
+            b.step(1)
