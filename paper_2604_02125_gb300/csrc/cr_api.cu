@@ -170,6 +170,15 @@ void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* plc)
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
   fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  lc.sms = 1;
+  cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev);
+}
+
+// whole 32-element tiles of the state can be fetched with 16-byte bulk copies
+int tma_ok_for(const double* u, long long E, int NP) {
+  return ((reinterpret_cast<size_t>(u) & 15) == 0 && ((E * NP) % 2) == 0) ? 1 : 0;
 }
 
 int default_epb(const VariantOps& o) {
@@ -301,6 +310,7 @@ static int init_single(cr_ctx* c) {
   al((void**)&lc.partials, sizeof(double) * c->partial_blocks);
   al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
   if (rc != CR_OK) { free_single(c); return rc; }
+  lc.ma.tma_ok = tma_ok_for(lc.u, E, o.NP);
   cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   CR_TRY(cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream));

@@ -149,6 +149,7 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
     lc.st = b->st + k;
     lc.partials = b->partials;
     lc.totals_part = b->totals_part;
+    lc.ma.tma_ok = tma_ok_for(lc.u, lc.ma.E, b->ops[k].NP);
     std::memset(&hs[k], 0, sizeof(BatchSolve));
     hs[k].ma = lc.ma;
     hs[k].u = lc.u;

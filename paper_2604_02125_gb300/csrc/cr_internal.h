@@ -20,7 +20,8 @@ struct LaunchCtx {
   PhysParams<float> pp32;
   RefTab<double> tb64;
   RefTab<float> tb32;
-  int epb;            // elements per CTA of the volume kernel
+  int epb;            // elements per CTA of the volume kernel (tile form)
+  int sms;            // multiprocessors of the device (persistent grids)
 };
 
 // One launch of a batched persistent kernel (all solves of one degree).
@@ -91,5 +92,8 @@ int default_epb(const VariantOps& o);
 
 // mesh arguments, physics parameters and tables of one descriptor (no allocation)
 void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* lc);
+
+// 1 if whole tiles of a state at u (E elements of NP nodes) can be bulk-copied
+int tma_ok_for(const double* u, long long E, int NP);
 
 }  // namespace crk

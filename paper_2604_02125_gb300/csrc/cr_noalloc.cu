@@ -124,6 +124,9 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
   fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
+  lc.sms = 1;
+  cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev);
+  lc.ma.tma_ok = tma_ok_for(u_out, E, o.NP);
 
   if ((e = o.set_smem(o.vol_smem(lc.epb))) != cudaSuccess) return to_status(e);
   if (u_out != u_in &&

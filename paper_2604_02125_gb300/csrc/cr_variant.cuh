@@ -3,6 +3,8 @@
 #include "cr_internal.h"
 #include "crkfr_volume_lanes.cuh"
 
+#include <algorithm>
+
 namespace crk {
 
 template <typename R> struct PP;
@@ -29,12 +31,27 @@ template <class EQ, int N, typename R>
 struct Variant {
   using L = VolLayout<EQ, N, R>;
   using LL = LaneLayout<EQ, N, R>;
-  static constexpr bool kLanes = LL::fits();
-  static size_t vol_smem(int epb) { return kLanes ? LL::bytes() : (size_t)epb * L::bytes_per_elem(); }
+  using PL = PersistLayout<EQ, N, R>;
+  static constexpr bool kLanes = PL::fits();
+  static size_t vol_smem(int epb) { return kLanes ? PL::bytes() : (size_t)epb * L::bytes_per_elem(); }
+  // resident CTAs per SM of the persistent volume kernel (computed once)
+  static int vol_occupancy() {
+    static int occ = -1;
+    if (occ < 0) {
+      int nb = 0;
+      if constexpr (kLanes) {
+        cudaFuncSetAttribute(k_volume_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_lanes<EQ, N, R>, LL::THREADS, PL::bytes());
+      }
+      occ = nb > 0 ? nb : 1;
+    }
+    return occ;
+  }
   static cudaError_t volume(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (kLanes) {
-      const long long grid = (c.ma.E + 31) / 32;
-      k_volume_lanes<EQ, N, R><<<(unsigned)grid, LL::THREADS, LL::bytes(), s>>>(
+      const long long ntiles = (c.ma.E + 31) / 32;
+      const long long grid = std::min(ntiles, (long long)c.sms * vol_occupancy());
+      k_volume_lanes<EQ, N, R><<<(unsigned)grid, LL::THREADS, PL::bytes(), s>>>(
           c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c));
     } else {
       const long long grid = (c.ma.E + c.epb - 1) / c.epb;
@@ -47,6 +64,7 @@ struct Variant {
   }
   using FL = FaceLaneLayout<EQ, N, R>;
   static constexpr bool kFaceLanes = FL::fits();
+  static constexpr bool kBatched = EQ::DIM == 2 && !EQ::NC && kLanes && kFaceLanes;
   static cudaError_t face_update(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (kFaceLanes) {
       const unsigned grid = (unsigned)((c.ma.E + 31) / 32);
@@ -73,15 +91,20 @@ struct Variant {
     return cudaGetLastError();
   }
   static cudaError_t set_smem(size_t bytes) {
-    if constexpr (kLanes)
+    if constexpr (kLanes) {
+      if constexpr (kBatched) {
+        cudaError_t e = cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PL::bytes());
+        if (e != cudaSuccess) return e;
+      }
       return cudaFuncSetAttribute(k_volume_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
     else
       return cudaFuncSetAttribute(k_volume_tile<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   }
-  static constexpr bool kBatched = EQ::DIM == 2 && !EQ::NC && kLanes && kFaceLanes;
   static cudaError_t vol_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
-      k_volume_batched<EQ, N, R><<<b.grid, LL::THREADS, LL::bytes(), s>>>(
+      k_volume_batched<EQ, N, R><<<b.grid, LL::THREADS, PL::bytes(), s>>>(
           b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b));
       return cudaGetLastError();
     }
@@ -99,8 +122,8 @@ struct Variant {
     int nb = 0;
     if constexpr (kBatched) {
       if (which == 0) {
-        cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LL::bytes());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batched<EQ, N, R>, LL::THREADS, LL::bytes());
+        cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batched<EQ, N, R>, LL::THREADS, PL::bytes());
       } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_face_batched<EQ, N, R>, FL::THREADS, 0);
       }

@@ -25,6 +25,7 @@
 //         one record of CP values per face node (C used, padded to 16 bytes):
 //         U (M), F^d (M), lambda_d(u^n) (1) [+ GLM-MHD: F^nc,d (M), u^n (M)]
 #pragma once
+#include "crkfr_async.cuh"
 #include "crkfr_physics.cuh"
 
 namespace crk {
@@ -59,6 +60,7 @@ struct MeshArgs {
   double cfl, dt_fixed;
   double gamma, c_h;
   float inv_dx_f[3], gamma_f, c_h_f;   // FP32 copies (no conversions on the FP64 pipe)
+  int tma_ok;           // state base 16-byte aligned and E * NP even: whole tiles can be bulk-copied
 };
 template <typename R> __device__ __forceinline__ R inv_dx_of(const MeshArgs& ma, int d);
 template <> __device__ __forceinline__ double inv_dx_of<double>(const MeshArgs& ma, int d) { return ma.inv_dx[d]; }

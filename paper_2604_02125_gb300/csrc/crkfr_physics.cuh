@@ -168,6 +168,15 @@ struct Euler {
     return q[0] * q[IAUX];
   }
 
+  // conserved variables from pair data
+  template <typename R>
+  __device__ __forceinline__ static void cons_from_pair(const R* q, R* u, const PhysParams<R>& pp) {
+    u[0] = q[0];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) u[1 + k] = q[0] * q[1 + k];
+    u[DIM + 1] = total_energy(q, pp);
+  }
+
   // physical flux in direction d from pair data
   template <typename R>
   __device__ __forceinline__ static void flux(int d, const R* q, R* f, const PhysParams<R>& pp) {
@@ -276,6 +285,16 @@ struct GlmMhd {
     q[5] = B1; q[6] = B2; q[7] = B3; q[8] = psi;
     q[IBETA] = R(0.5) * rho * fast_rcp(p);
     q[IV2] = vv; q[IB2] = BB; q[IVB] = v1 * B1 + v2 * B2 + v3 * B3;
+  }
+
+  // conserved variables from pair data
+  template <typename R>
+  __device__ __forceinline__ static void cons_from_pair(const R* q, R* u, const PhysParams<R>& pp) {
+    const R rho = q[0];
+    u[0] = rho;
+    u[1] = rho * q[1]; u[2] = rho * q[2]; u[3] = rho * q[3];
+    u[4] = q[IP] * pp.inv_gm1 + R(0.5) * (rho * q[IV2] + q[IB2] + q[IPSI] * q[IPSI]);
+    u[5] = q[5]; u[6] = q[6]; u[7] = q[7]; u[8] = q[8];
   }
 
   template <typename R>

@@ -39,20 +39,21 @@ __host__ __device__ constexpr int rk_nsaved(int N) { return rk_slot(N, rk_stages
 // end points of a GLL line, where D_pp is non-zero.
 template <class EQ, int N, typename R, int D>
 __device__ __forceinline__ void line_residual(const R (&q)[N + 1][EQ::P], R (&acc)[N + 1][EQ::M],
-                                              const PhysParams<R>& pp, const RefTab<R>& tb, R inv_dx) {
+                                              R (&fend)[2][EQ::M], const PhysParams<R>& pp, const RefTab<R>& tb,
+                                              R inv_dx) {
   constexpr int n = N + 1, M = EQ::M;
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
     for (int v = 0; v < M; ++v) acc[k][v] = R(0);
-  {
-    R f[M];
-    EQ::flux(D, q[0], f, pp);
+  // physical fluxes at the two end points: the D_pp terms here, and the face
+  // sums of the time-averaged flux (eq. disc.avg.flux) in the caller
+  EQ::flux(D, q[0], fend[0], pp);
+  EQ::flux(D, q[N], fend[1], pp);
 #pragma unroll
-    for (int v = 0; v < M; ++v) acc[0][v] = R(2) * tb.D[0][0] * f[v];
-    EQ::flux(D, q[N], f, pp);
-#pragma unroll
-    for (int v = 0; v < M; ++v) acc[N][v] = R(2) * tb.D[N][N] * f[v];
+  for (int v = 0; v < M; ++v) {
+    acc[0][v] = R(2) * tb.D[0][0] * fend[0][v];
+    acc[N][v] = R(2) * tb.D[N][N] * fend[1][v];
   }
 #pragma unroll
   for (int a = 0; a < n; ++a)
@@ -88,34 +89,130 @@ template <class EQ, int N, typename R>
 struct LaneLayout {
   static constexpr int DIM = EQ::DIM, M = EQ::M, P = EQ::P, n = N + 1;
   static constexpr int NP = ipow(n, DIM), NF = NP / n, S = rk_stages(N);
-  static constexpr int FACE = DIM * M * 2 * NF;            // [DIM][M][2][NF]
-  static constexpr int O_Q = 0;                            // [P][NP] pair data (also staging)
-  static constexpr int O_RY = O_Q + P * NP;                // [M][NP] y (+z) residual
-  static constexpr int O_UB = O_RY + (DIM > 1 ? M * NP : 0);   // [M][NP] time-averaged U (face nodes)
-  static constexpr int O_FB = O_UB + M * NP;               // time-averaged F^d at d-faces
-  static constexpr int O_FN = O_FB + FACE;                 // GLM-MHD: time-averaged F^nc,d
-  static constexpr int O_UN = O_FN + (EQ::NC ? FACE : 0);  // GLM-MHD: u^n at d-faces
-  static constexpr int O_LAM = O_UN + (EQ::NC ? FACE : 0); // [DIM][2][NF] lambda_d(u^n)
-  static constexpr int SZ0 = O_LAM + DIM * 2 * NF;
-  static constexpr int SZ = SZ0 | 1;                       // odd element stride: no bank conflicts
+  static constexpr int O_Q = 0;                                // [P][NP] pair data (also staging)
+  static constexpr int O_RY = O_Q + P * NP;                    // [M][NP] y (+z) residual
+  static constexpr int O_U0 = O_RY + (DIM > 1 ? M * NP : 0);   // [M][NP] u^n
+  static constexpr int SZ0 = O_U0 + M * NP;
+  static constexpr int SZ = SZ0 | 1;                           // odd element stride: no bank conflicts
   static constexpr int EPB = 32;
   static constexpr int THREADS = 32 * NF;
   static constexpr size_t bytes() { return sizeof(R) * (size_t)SZ * EPB; }
-  // CTAs per SM the register allocation aims at (Euler with small lines:
-  // 5 x 128 threads = 20 warps; larger variants are limited by registers anyway)
-  static constexpr int MINB = (!EQ::NC && THREADS <= 128) ? 5 : 1;
+  // CTAs per SM the register allocation aims at
+  static constexpr int MINB = (!EQ::NC && THREADS <= 128) ? 4 : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
 };
 
+// Time averages at the two end points of one line in direction D (the face
+// nodes of the two faces normal to D): U = sum_i b_i u^(i), F^D = sum_i b_i
+// f^D(u^(i)) (eq. disc.avg.flux), lambda_D(u^n), and for the non-conservative
+// system F^nc,D = sum_i b_i B^D g^D (Sec. 2.3).  One record per end.
+template <class EQ, typename R>
+struct FaceAcc {
+  static constexpr int M = EQ::M;
+  R U[2][M], F[2][M], lam[2];
+  R Nc[EQ::NC ? 2 : 1][M];
+};
+
+template <class EQ, int N, typename R, int D>
+__device__ __forceinline__ void face_accumulate(FaceAcc<EQ, R>& fa, const R (&q)[N + 1][EQ::P],
+                                                const R (&fend)[2][EQ::M], R b, bool first,
+                                                const PhysParams<R>& pp) {
+  constexpr int M = EQ::M;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const R* qs = q[side ? N : 0];
+    R uu[M];
+    EQ::cons_from_pair(qs, uu, pp);
+    if (first) {
+      fa.lam[side] = EQ::wave_speed(D, qs, pp);
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        fa.U[side][v] = R(0);
+        fa.F[side][v] = R(0);
+      }
+      if constexpr (EQ::NC) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) fa.Nc[side][v] = R(0);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      fa.U[side][v] += b * uu[v];
+      fa.F[side][v] += b * fend[side][v];
+    }
+    if constexpr (EQ::NC) {
+      R g[2], nc[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) nc[v] = R(0);
+      EQ::ncg(D, qs, g);
+      EQ::nc_apply(D, qs, g, nc);
+#pragma unroll
+      for (int v = 0; v < M; ++v) fa.Nc[side][v] += b * nc[v];
+    }
+  }
+}
+
+// Record of one face node: U, F, lambda [, F^nc, u^n], padded to CP.  u^n of
+// the two end nodes (non-conservative system) is read from shared memory:
+// un0 / unN point at variable 0 of the end nodes, variables NP apart.
+template <class EQ, typename R>
+__device__ __forceinline__ void write_records(R* __restrict__ trace, const FaceAcc<EQ, R>& fa, int d, int NFv,
+                                              long long E, long long e, int f, const R* un0, const R* unN,
+                                              int NPv) {
+  constexpr int M = EQ::M, C = trace_comps<EQ>(), CP = trace_stride<EQ, R>();
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    R rec[CP];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      rec[v] = fa.U[side][v];
+      rec[M + v] = fa.F[side][v];
+    }
+    rec[2 * M] = fa.lam[side];
+    if constexpr (EQ::NC) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        rec[2 * M + 1 + v] = fa.Nc[side][v];
+        rec[3 * M + 1 + v] = (side ? unN : un0)[v * NPv];
+      }
+    }
+#pragma unroll
+    for (int c = C; c < CP; ++c) rec[c] = R(0);
+    store_record<R, CP>(trace + ((((size_t)(d * 2 + side) * NFv + f) * E) + e) * CP, rec);
+  }
+}
+
+// Prefetch of the next tile's u^n into the staging buffer (TMA bulk copies,
+// one per variable), issued by thread 0 once the current tile's staging data
+// has been consumed.  src == nullptr: nothing to prefetch.
+struct Prefetch {
+  const double* src;        // u^n of variable 0 of the next tile
+  long long var_stride;     // doubles between variables (E * NP of the next tile's solve)
+  unsigned bytes;           // bytes per variable (32 * NP * 8)
+  double* staging;
+  unsigned long long* bar;
+};
+
+template <int M>
+__device__ __forceinline__ void issue_prefetch(const Prefetch& pf) {
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(pf.bar, M * pf.bytes);
+#pragma unroll
+  for (int v = 0; v < M; ++v)
+    bulk_copy_g2s(pf.staging + (size_t)v * (pf.bytes / 8), pf.src + (size_t)v * pf.var_stride, pf.bytes, pf.bar);
+}
+
 // One tile of 32 elements starting at e0 (the CTA's whole shared memory sm).
+// staged != nullptr: u^n of the tile already sits in shared memory as FP64,
+// [var][32][NP] (the tile's slice of the global layout).
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
                                                   R* __restrict__ trace, const DevState* __restrict__ st,
                                                   const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
-                                                  long long e0, R* sm) {
+                                                  long long e0, R* sm, const double* staged = nullptr,
+                                                  Prefetch pf = Prefetch{nullptr, 0, 0, nullptr, nullptr}) {
   using L = LaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
-  constexpr int C = trace_comps<EQ>();
   constexpr int NS = rk_nsaved(N) > 0 ? rk_nsaved(N) : 1;
 
   const int tid = threadIdx.x;
@@ -130,13 +227,6 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
   else dtR = st->dt_next;
 
-  // coordinates of this thread's x-line in the other directions (warp-uniform)
-  int cy = 0, cz = 0;
-  if (DIM >= 2) cy = l % n;
-  if (DIM == 3) cz = l / n;
-  const bool yface = DIM >= 2 && (cy == 0 || cy == N);
-  const bool zface = DIM == 3 && (cz == 0 || cz == N);
-
   // ---- u^n: coalesced into shared memory (staging in the Q region), then own x-line to registers
   // (index arithmetic with compile-time divisors only)
 #pragma unroll 4
@@ -145,30 +235,29 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     const int v = idx / (32 * NP), r = idx % (32 * NP);
     const int ee = r / NP, p = r % NP;
     if (v < M && ee < nel) {
-      const double x = u[((size_t)v * E + e0) * NP + r];
-      if constexpr (sizeof(R) == 4) sm[(size_t)ee * L::SZ + L::O_Q + v * NP + p] = d2f_int(x);
-      else sm[(size_t)ee * L::SZ + L::O_Q + v * NP + p] = x;
+      const double x = staged ? staged[(size_t)v * 32 * NP + r] : u[((size_t)v * E + e0) * NP + r];
+      if constexpr (sizeof(R) == 4) sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = d2f_int(x);
+      else sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = x;
     }
   }
   __syncthreads();
-  R u0[n][M];
-#pragma unroll
-  for (int k = 0; k < n; ++k)
-#pragma unroll
-    for (int v = 0; v < M; ++v) u0[k][v] = active ? my[L::O_Q + v * NP + l * n + k] : R(1);
-  __syncthreads();
+  // the staging buffer is free: start the next tile's copy, overlapped with this tile's work
+  if (pf.src && tid == 0) issue_prefetch<M>(pf);
 
   R rb[n][M], ax[n][M], rs[NS][n][M];
 #pragma unroll
   for (int k = 0; k < n; ++k)
 #pragma unroll
     for (int v = 0; v < M; ++v) { rb[k][v] = R(0); ax[k][v] = R(0); }
+  // face sums of the ends of this thread's x-line (faces normal to x), y-line and z-line
+  FaceAcc<EQ, R> fx, fy, fz;
 
   // the stage loop stays rolled: one stage's code is large, and S copies of it
   // would overflow the instruction cache; the tableau comes from the parameters
 #pragma unroll 1
   for (int i = 0; i < S; ++i) {
-    // ---------------- node phase (own x-line)
+    const R bi = tb.b[i];
+    // ---------------- node phase (own x-line): stage state and pair data
     R q[n][P];
     if (active) {
 #pragma unroll
@@ -189,77 +278,31 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
                 if (tb.slot[j] >= 0) acc += tb.a[i][j] * rs[tb.slot[j]][k][v];
             }
           }
-          uu[v] = u0[k][v] - dtR * acc;
+          uu[v] = my[L::O_U0 + v * NP + p] - dtR * acc;
         }
         EQ::pair_data(uu, q[k], pp);
         if (DIM > 1) {
 #pragma unroll
           for (int c = 0; c < P; ++c) my[L::O_Q + c * NP + p] = q[k][c];
         }
-        // face sums of the time averages: x faces at k = 0, N; y/z faces per line
-        const bool xf = (k == 0 || k == N);
-        const bool onface = xf || yface || zface;
-        if (i == 0 && onface) {
-          if (xf) my[L::O_LAM + (0 * 2 + (k == N)) * NF + l] = EQ::wave_speed(0, q[k], pp);
-          if (yface) my[L::O_LAM + (1 * 2 + (cy == N)) * NF + (k + n * cz)] = EQ::wave_speed(1, q[k], pp);
-          if (zface) my[L::O_LAM + (2 * 2 + (cz == N)) * NF + (k + n * cy)] = EQ::wave_speed(DIM - 1, q[k], pp);
-          if constexpr (EQ::NC) {
-#pragma unroll
-            for (int v = 0; v < M; ++v) {
-              if (xf) my[L::O_UN + ((0 * M + v) * 2 + (k == N)) * NF + l] = uu[v];
-              if (yface) my[L::O_UN + ((1 * M + v) * 2 + (cy == N)) * NF + k] = uu[v];
-            }
-          }
-        }
-        const R b = tb.b[i];
-        if (b != R(0) && onface) {
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            R* ub = &my[L::O_UB + v * NP + p];
-            *ub = (i == 0 ? R(0) : *ub) + b * uu[v];
-          }
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            bool on = d == 0 ? xf : d == 1 ? yface : zface;
-            if (!on) continue;
-            const int side = d == 0 ? (k == N) : d == 1 ? (cy == N) : (cz == N);
-            const int f = d == 0 ? l : d == 1 ? (k + n * cz) : (k + n * cy);
-            R fl[M];
-            EQ::flux(d, q[k], fl, pp);
-#pragma unroll
-            for (int v = 0; v < M; ++v) {
-              R* fb = &my[L::O_FB + ((d * M + v) * 2 + side) * NF + f];
-              *fb = (i == 0 ? R(0) : *fb) + b * fl[v];
-            }
-            if constexpr (EQ::NC) {
-              R g[2], nc[M];
-#pragma unroll
-              for (int v = 0; v < M; ++v) nc[v] = R(0);
-              EQ::ncg(d, q[k], g);
-              EQ::nc_apply(d, q[k], g, nc);
-#pragma unroll
-              for (int v = 0; v < M; ++v) {
-                R* fn = &my[L::O_FN + ((d * M + v) * 2 + side) * NF + f];
-                *fn = (i == 0 ? R(0) : *fn) + b * nc[v];
-              }
-            }
-          }
-        }
       }
       // ---------------- x-direction flux differencing, all in registers
-      line_residual<EQ, N, R, 0>(q, ax, pp, tb, inv_dx_of<R>(ma, 0));
+      R fend[2][M];
+      line_residual<EQ, N, R, 0>(q, ax, fend, pp, tb, inv_dx_of<R>(ma, 0));
+      face_accumulate<EQ, N, R, 0>(fx, q, fend, bi, i == 0, pp);
     }
     if (DIM > 1) {
       __syncthreads();   // Q of this stage visible; RY of the last stage consumed
       if (active) {
         // y-line l: nodes (i = l % n, j = 0..N, k = l / n)
         const int base = (l % n) + (l / n) * n * n;
-        R qy[n][P], ay[n][M];
+        R qy[n][P], ay[n][M], fend[2][M];
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < P; ++c) qy[k][c] = my[L::O_Q + c * NP + base + k * n];
-        line_residual<EQ, N, R, (DIM > 1 ? 1 : 0)>(qy, ay, pp, tb, inv_dx_of<R>(ma, 1));
+        line_residual<EQ, N, R, (DIM > 1 ? 1 : 0)>(qy, ay, fend, pp, tb, inv_dx_of<R>(ma, 1));
+        face_accumulate<EQ, N, R, (DIM > 1 ? 1 : 0)>(fy, qy, fend, bi, i == 0, pp);
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -270,12 +313,13 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         if (active) {
           // z-line l: nodes (i, j) = (l % n, l / n), k = 0..N
           const int base = l;
-          R qz[n][P], az[n][M];
+          R qz[n][P], az[n][M], fend[2][M];
 #pragma unroll
           for (int k = 0; k < n; ++k)
 #pragma unroll
             for (int c = 0; c < P; ++c) qz[k][c] = my[L::O_Q + c * NP + base + k * n * n];
-          line_residual<EQ, N, R, DIM - 1>(qz, az, pp, tb, inv_dx_of<R>(ma, DIM - 1));
+          line_residual<EQ, N, R, DIM - 1>(qz, az, fend, pp, tb, inv_dx_of<R>(ma, DIM - 1));
+          face_accumulate<EQ, N, R, DIM - 1>(fz, qz, fend, bi, i == 0, pp);
 #pragma unroll
           for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -306,47 +350,69 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     const int ee = r / NP, p = r % NP;
     if (v < M && ee < nel) rbar[((size_t)v * E + e0) * NP + r] = sm[(size_t)ee * L::SZ + L::O_Q + v * NP + p];
   }
-  // ---- face traces [DIM][2][NF][E][CP]: thread (warp l, lane el) writes the
-  // record of face node f = l of element el, CP values with 16-byte stores;
-  // consecutive lanes write consecutive records
-  constexpr int CP = trace_stride<EQ, R>();
+  // ---- face records [DIM][2][NF][E][CP]: this thread owns the two ends of its
+  // x-, y- and z-line, i.e. face node f = l of every face; consecutive lanes
+  // write consecutive records
   if (active) {
-    const int f = l;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int stride = ipow(n, d);
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int p = line_base<n>(f, stride) + side * N * stride;
-        R rec[CP];
-#pragma unroll
-        for (int v = 0; v < M; ++v) {
-          rec[v] = my[L::O_UB + v * NP + p];
-          rec[M + v] = my[L::O_FB + ((d * M + v) * 2 + side) * NF + f];
-        }
-        rec[2 * M] = my[L::O_LAM + (d * 2 + side) * NF + f];
-        if constexpr (EQ::NC) {
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            rec[2 * M + 1 + v] = my[L::O_FN + ((d * M + v) * 2 + side) * NF + f];
-            rec[3 * M + 1 + v] = my[L::O_UN + ((d * M + v) * 2 + side) * NF + f];
-          }
-        }
-#pragma unroll
-        for (int c = C; c < CP; ++c) rec[c] = R(0);
-        store_record<R, CP>(trace + ((((size_t)(d * 2 + side) * NF + f) * E) + e0 + el) * CP, rec);
-      }
-    }
+    const R* u0 = my + L::O_U0;
+    // end nodes: x-line l (l n, l n + N), y-line l (by, by + N n), z-line l (l, l + N n^2)
+    const int by = (l % n) + (l / n) * n * n;
+    write_records<EQ, R>(trace, fx, 0, NF, E, e0 + el, l, u0 + l * n, u0 + l * n + N, NP);
+    if (DIM > 1) write_records<EQ, R>(trace, fy, 1, NF, E, e0 + el, l, u0 + by, u0 + by + N * n, NP);
+    if (DIM > 2) write_records<EQ, R>(trace, fz, 2, NF, E, e0 + el, l, u0 + l, u0 + l + N * n * n, NP);
   }
 }
 
+// shared memory of the persistent lane kernels: lane layout, then the FP64
+// staging buffer of one tile, then the mbarrier
+template <class EQ, int N, typename R>
+struct PersistLayout {
+  using L = LaneLayout<EQ, N, R>;
+  static constexpr size_t O_STAGE = (L::bytes() + 15) & ~(size_t)15;
+  static constexpr size_t STAGE_BYTES = sizeof(double) * (size_t)EQ::M * 32 * L::NP;
+  static constexpr size_t O_BAR = O_STAGE + STAGE_BYTES;
+  static constexpr size_t bytes() { return O_BAR + 16; }
+  static constexpr bool fits() { return L::fits() && bytes() <= 227 * 1024; }
+};
+
+// Persistent volume kernel for one solve: CTA b handles tiles b, b + grid, ...;
+// u^n of whole tiles arrives by TMA bulk copy one tile ahead.
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
 k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
                DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+  using PL = PersistLayout<EQ, N, R>;
+  constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)blockIdx.x * 32,
-                              reinterpret_cast<R*>(smem_raw));
+  R* sm = reinterpret_cast<R*>(smem_raw);
+  double* staging = reinterpret_cast<double*>(smem_raw + PL::O_STAGE);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + PL::O_BAR);
+  const long long E = ma.E;
+  const unsigned ntiles = (unsigned)((E + 31) / 32);
+  auto whole = [&](unsigned t) { return ma.tma_ok && (long long)(t + 1) * 32 <= E; };
+  auto pf_of = [&](unsigned t) {
+    return Prefetch{u + (size_t)t * 32 * NP, E * NP, (unsigned)(32 * NP * sizeof(double)), staging, bar};
+  };
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  unsigned phase = 0;
+  unsigned t = blockIdx.x;
+  if (t < ntiles && whole(t) && threadIdx.x == 0) issue_prefetch<M>(pf_of(t));
+  for (; t < ntiles; t += gridDim.x) {
+    const bool staged = whole(t);
+    if (staged) {
+      const bool ok = mbar_wait_bounded(bar, phase);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(&st->status, ST_TIMEOUT);
+        return;
+      }
+      phase ^= 1u;
+    }
+    const unsigned tn = t + gridDim.x;
+    const Prefetch pf = (tn < ntiles && whole(tn)) ? pf_of(tn) : Prefetch{nullptr, 0, 0, nullptr, nullptr};
+    volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, sm, staged ? staging : nullptr, pf);
+    __syncthreads();   // shared memory is reused by the next tile
+  }
 }
 
 }  // namespace crk
@@ -520,12 +586,48 @@ template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
 k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
                  const PhysParams<R> pp, const RefTab<R> tb) {
+  using PL = PersistLayout<EQ, N, R>;
+  constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x) {
+  R* sm = reinterpret_cast<R*>(smem_raw);
+  double* staging = reinterpret_cast<double*>(smem_raw + PL::O_STAGE);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + PL::O_BAR);
+  auto whole = [&](const BatchTile& t) {
+    const BatchSolve& bs = solves[t.solve];
+    return bs.ma.tma_ok && (long long)t.e0 + 32 <= bs.ma.E;
+  };
+  auto pf_of = [&](const BatchTile& t) {
+    const BatchSolve& bs = solves[t.solve];
+    return Prefetch{bs.u + (size_t)t.e0 * NP, bs.ma.E * NP, (unsigned)(32 * NP * sizeof(double)), staging, bar};
+  };
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  unsigned phase = 0;
+  unsigned it = blockIdx.x;
+  if (it < ntiles && threadIdx.x == 0) {
+    const BatchTile t0 = tiles[it];
+    if (whole(t0)) issue_prefetch<M>(pf_of(t0));
+  }
+  for (; it < ntiles; it += gridDim.x) {
     const BatchTile t = tiles[it];
-    const MeshArgs ma = solves[t.solve].ma;
-    volume_lanes_tile<EQ, N, R>(solves[t.solve].u, (R*)solves[t.solve].rbar, (R*)solves[t.solve].trace,
-                                solves[t.solve].st, ma, pp, tb, (long long)t.e0, reinterpret_cast<R*>(smem_raw));
+    const BatchSolve& bs = solves[t.solve];
+    const bool staged = whole(t);
+    if (staged) {
+      const bool ok = mbar_wait_bounded(bar, phase);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicOr(&bs.st->status, ST_TIMEOUT);
+        return;
+      }
+      phase ^= 1u;
+    }
+    Prefetch pf{nullptr, 0, 0, nullptr, nullptr};
+    if (it + gridDim.x < ntiles) {
+      const BatchTile tn = tiles[it + gridDim.x];
+      if (whole(tn)) pf = pf_of(tn);
+    }
+    const MeshArgs ma = bs.ma;
+    volume_lanes_tile<EQ, N, R>(bs.u, (R*)bs.rbar, (R*)bs.trace, bs.st, ma, pp, tb, (long long)t.e0, sm,
+                                staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }
 }
