@@ -74,7 +74,8 @@ class ClockSampler:
         self.proc = None
         self.out = None
 
-    def start(self):
+    def start(self, wait_s=3.0):
+        """Start sampling; returns once the first sample is in (or after wait_s)."""
         try:
             self.out = open(os.path.join(ROOT, ".clocks_%d.csv" % os.getpid()), "w+")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
@@ -82,6 +83,13 @@ class ClockSampler:
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < wait_s and self.proc.poll() is None:
+            self.out.flush()
+            if os.path.getsize(self.out.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -111,6 +119,24 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def job_time_ms(local_ms, world, dist=None, device="cuda"):
+    """Whole-job time of a timed region: the maximum over ranks."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(nodes_per_rank, steps, world, job_ms):
+    """DOF-updates/s of the whole job: every rank advances its own replica."""
+    return world * nodes_per_rank * steps / (job_ms * 1e-3)
+
+
+VOLUME_PROFILE = os.path.join(ROOT, "profiles", "k_volume_lanes_shear2d_256x256_N3_fp32.md")
 
 
 def time_steps(solver, steps, stream, flush):
@@ -239,19 +265,16 @@ def main():
         s32.set_state(U)
         s32.step(args.warmup)
         s32.sync()
+        # clocks are sampled from just before the first timed region to the
+        # end of the last one (headline, FP64 form, batched form, per kernel)
         clk = ClockSampler(local)
         clk.start()
         barrier()
         times = time_steps(s32, args.steps, stream, flush)
         barrier()
-        clocks = clk.stop()
         status = s32.info()["status"]
-        total_ms = sum(times)
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * nodes * args.steps / (total_ms * 1e-3)
+        total_ms = job_time_ms(sum(times), world, dist)
+        value = job_value(nodes, args.steps, world, total_ms)
 
         # plain FP64 form, same workload, a few steps
         k64 = max(3, min(30, args.steps))
@@ -280,6 +303,7 @@ def main():
         # volume-kernel duration, CUDA events on the solver's stream, same L2 flush
         kv = max(3, min(50, args.steps))
         vol_ms, face_ms = s32.time_kernels(kv, flush)
+        clocks = clk.stop()
 
         # end to end through the C ABI with host buffers
         Uh = torch.from_numpy(U).pin_memory()
@@ -308,10 +332,15 @@ def main():
     ms_step = total_ms / args.steps
     roofline = None
     if vol_ms:
+        from paper_2604_02125_gb300 import profile_summary
+        prof = profile_summary.read_profile_traffic(VOLUME_PROFILE)
         ach = vflops / (vol_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                    "traffic": None, "kernel": "k_volume<Euler<2>,3,float>", "ms_per_launch": vol_ms,
-                    "face_update_ms_per_launch": face_ms}
+                    "peak_source": "FP32 lanes x max SM clock: 152 SMs x 128 lanes x 2 flops x %.0f MHz" % sm_mhz_max,
+                    "traffic": prof[1] if prof else None,
+                    "traffic_source": os.path.relpath(VOLUME_PROFILE, ROOT) if prof else "no capture of these sources",
+                    "kernel": "k_volume_lanes<Euler<2>,3,float>", "flops_per_launch": vflops,
+                    "ms_per_launch": vol_ms, "face_update_ms_per_launch": face_ms}
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -328,7 +357,7 @@ def main():
         "e2e": {"value": world * nodes * ke / e2e_s, "unit": "DOF-updates/s",
                 "h2d_bytes_per_step": int(U.nbytes), "d2h_bytes_per_step": int(U.nbytes)},
         "roofline": roofline,
-        "clocks": clocks,
+        "clocks": dict(clocks, window="headline, fp64, batched and per-kernel timed regions") if clocks else None,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()

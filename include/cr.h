@@ -140,6 +140,17 @@ int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes
  * 2 GiB allocated for the call).  Synchronises the device. */
 int cr_probe_peak(int kind, double *result);
 
+/* Self-check of the FP32 form's float <-> double conversions, which use
+ * integer instructions instead of the hardware conversion (on this GPU the
+ * hardware conversion runs on the narrow FP64 pipe).  The paper has no
+ * counterpart.  Converts n seeded bit patterns (half of the doubles with
+ * exponents confined to the FP32 range and its edges, plus infinities and
+ * NaNs) both ways on the current device and stores in *mismatches how many
+ * results differ from the hardware conversion; inputs below the normal FP32
+ * range are expected to give signed zero.  Returns CR_EINVAL for n < 0 or a
+ * NULL pointer, CR_ENOMEM/CR_ECUDA on a device error.  Synchronises. */
+int cr_check_conversions(long long n, unsigned long long seed, long long *mismatches);
+
 /* One time step without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while they advance a solve -- an application whose memory

@@ -39,7 +39,7 @@ _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
            "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
-           "cr_probe_peak", "cr_tuning_info")
+           "cr_probe_peak", "cr_tuning_info", "cr_check_conversions")
 
 
 def load_library(path=None):
@@ -64,6 +64,7 @@ def load_library(path=None):
     lib.cr_step_noalloc.argtypes = [ctypes.POINTER(MeshDesc), vp, vp, vp, vp]
     lib.cr_probe_peak.argtypes = [ip, dp]
     lib.cr_tuning_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.cr_check_conversions.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -265,3 +266,12 @@ def _current_torch_stream():
     except Exception:
         pass
     return 0
+
+
+def check_conversions(n=1 << 24, seed=2604021255):
+    """Mismatches of the FP32 form's integer float<->double conversions against
+    the hardware conversions over n seeded bit patterns (0 expected)."""
+    lib = load_library()
+    r = ctypes.c_longlong(-1)
+    _check(lib.cr_check_conversions(int(n), int(seed), ctypes.byref(r)), "cr_check_conversions")
+    return int(r.value)

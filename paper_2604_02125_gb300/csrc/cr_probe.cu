@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/cr.h"
+#include "crkfr_physics.cuh"
 
 namespace {
 
@@ -81,7 +82,69 @@ __global__ void __launch_bounds__(256) p_copy(const float4* __restrict__ a, floa
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = a[i];
 }
 
+// splitmix64 (Steele, Lea, Flood 2014) of a counter: test bit patterns
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Integer conversions of the FP32 form against the hardware conversions.
+// Pattern k: a random double (odd k: exponent confined to the FP32 range and
+// its edges) and a random float bit pattern.  Inputs below the normal FP32
+// range must give signed zero (the documented flush); every other input the
+// hardware's result bit for bit (NaN: any NaN).
+__global__ void __launch_bounds__(256) k_check_cvt(long long n, unsigned long long seed,
+                                                   unsigned long long* bad) {
+  unsigned long long cnt = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = mix64(seed ^ mix64((unsigned long long)k));
+    unsigned long long db = r;
+    if (k & 1) {
+      const unsigned long long e = 870ull + (r >> 52) % 300ull;   // 870..1169
+      db = (r & 0x800FFFFFFFFFFFFFull) | (e << 52);
+    }
+    if ((k & 15) == 2) db = (r & 0x8000000000000000ull) | 0x7FF0000000000000ull | ((k & 16) ? (r & 0xFFFFFull) : 0ull);
+    const double x = __longlong_as_double((long long)db);
+    const float hw = __double2float_rn(x), mine = crk::d2f_int(x);
+    const bool below = fabs(x) < 1.1754943508222875e-38;   // 2^-126
+    bool ok;
+    if (x != x) ok = mine != mine;
+    else if (below) ok = __float_as_uint(mine) == (unsigned)((db >> 32) & 0x80000000ull);
+    else ok = __float_as_uint(mine) == __float_as_uint(hw);
+    const unsigned fb = (unsigned)(r >> 17);
+    const float f = __uint_as_float(fb);
+    const double hwd = (double)f, mined = crk::f2d_int(f);
+    bool okd;
+    if (f != f) okd = mined != mined;
+    else if (((fb >> 23) & 0xFFu) == 0u) okd = __double_as_longlong(mined) == (long long)((unsigned long long)(fb & 0x80000000u) << 32);
+    else okd = __double_as_longlong(mined) == __double_as_longlong(hwd);
+    cnt += (ok ? 0u : 1u) + (okd ? 0u : 1u);
+  }
+  if (cnt) atomicAdd(bad, cnt);
+}
+
 }  // namespace
+
+extern "C" int cr_check_conversions(long long n, unsigned long long seed, long long* mismatches) {
+  if (!mismatches || n < 0) return CR_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CR_ENODEV;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CR_ECUDA;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return CR_ENOMEM;
+  unsigned long long h = 0;
+  int rc = CR_OK;
+  if (cudaMemset(d, 0, sizeof(h)) != cudaSuccess) rc = CR_ECUDA;
+  if (rc == CR_OK && n > 0) k_check_cvt<<<sms * 8, 256>>>(n, seed, d);
+  if (rc == CR_OK && (cudaGetLastError() != cudaSuccess ||
+                      cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess))
+    rc = CR_ECUDA;
+  cudaFree(d);
+  if (rc == CR_OK) *mismatches = (long long)h;
+  return rc;
+}
 
 extern "C" int cr_probe_peak(int kind, double* result) {
   if (!result || kind < 0 || kind > 5) return CR_EINVAL;

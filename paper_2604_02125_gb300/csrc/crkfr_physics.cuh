@@ -100,28 +100,45 @@ __device__ __forceinline__ void logmean_pair(R a1, R b1, R a2, R b2, R& L1, R& i
   }
 }
 
-// Exact float <-> double conversions with integer instructions (the FP64 pipe
-// of this GPU is narrow and also executes the hardware conversions).  Values
-// below the normal FP32 range become signed zero; infinities, NaNs and values
-// above the FP32 range take the hardware conversion.
+// Exact float <-> double conversions with integer instructions only (the FP64
+// pipe of this GPU is narrow and also executes the hardware conversions, and a
+// predicated hardware fallback would still occupy it).  Values below the
+// normal FP32 range become signed zero; overflow gives a signed infinity,
+// NaN stays NaN.
 __device__ __forceinline__ float d2f_int(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7FFu;
-  if (e < 897u) return __uint_as_float(hi & 0x80000000u);
-  if (e > 1150u) return (float)x;
+  const unsigned sign = hi & 0x80000000u;
   const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1FFFFFFFu;
-  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | mant;
+  unsigned bits = sign | ((e - 896u) << 23) | mant;
   bits += (rest > 0x10000000u) | ((rest == 0x10000000u) & (mant & 1u));   // round to nearest even
+  const bool nan = e == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u;
+  bits = e < 897u ? sign : bits;
+  bits = e > 1150u ? (sign | 0x7F800000u | (nan ? 0x400000u : 0u)) : bits;
   return __uint_as_float(bits);
 }
 __device__ __forceinline__ double f2d_int(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned e = (b >> 23) & 0xFFu;
-  if (e == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  if (e == 255u) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned ed = e == 255u ? 0x7FFu : e + 896u;
+  unsigned hi = (b & 0x80000000u) | (ed << 20) | ((b & 0x7FFFFFu) >> 3);
+  unsigned lo = b << 29;
+  hi = e == 0u ? (b & 0x80000000u) : hi;
+  lo = e == 0u ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Reciprocal and square root of the CFL wave speeds: IEEE in FP64, the MUFU
+// approximations (about 1 ulp) in FP32, where the result only enters the
+// maximum that sets dt.
+__device__ __forceinline__ double speed_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float speed_rcp(float x) { return fast_rcp(x); }
+__device__ __forceinline__ double speed_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float speed_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -244,9 +261,9 @@ struct Euler {
     T ke = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) ke += u[1 + k] * u[1 + k];
-    T ir = T(1) / rho;
+    T ir = speed_rcp(rho);
     T p = (gamma - T(1)) * (u[DIM + 1] - T(0.5) * ke * ir);
-    T c = sqrt(gamma * p * ir);
+    T c = speed_sqrt(gamma * p * ir);
     T s = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) s += (fabs(u[1 + k] * ir) + c) * inv_dx[k];
@@ -384,7 +401,7 @@ struct GlmMhd {
   template <typename T>
   __device__ __forceinline__ static bool physical(const T* u, T gamma, T c_h, T& lam_sum, const T* inv_dx) {
     T rho = u[0];
-    T ir = T(1) / rho;
+    T ir = speed_rcp(rho);
     T v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
     T BB = u[5] * u[5] + u[6] * u[6] + u[7] * u[7];
     T p = (gamma - T(1)) * (u[4] - T(0.5) * rho * (v1 * v1 + v2 * v2 + v3 * v3) - T(0.5) * BB - T(0.5) * u[8] * u[8]);
@@ -394,7 +411,7 @@ struct GlmMhd {
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       T bd2 = u[5 + d] * u[5 + d] * ir;
-      T cf = sqrt(T(0.5) * (s + sqrt(fmax(s * s - T(4) * a2 * bd2, T(0)))));
+      T cf = speed_sqrt(T(0.5) * (s + speed_sqrt(fmax(s * s - T(4) * a2 * bd2, T(0)))));
       tot += (fabs(vv[d]) + fmax(cf, c_h)) * inv_dx[d];
     }
     lam_sum = tot;
