@@ -100,6 +100,27 @@ __device__ __forceinline__ void logmean_pair(R a1, R b1, R a2, R b2, R& L1, R& i
   }
 }
 
+// FP32: 1/F(u) = sqrt(u)/artanh(sqrt(u)) by its own series (six terms; the
+// truncation is below 3e-10 relative for u < 0.05), so that the series branch
+// needs a single reciprocal: 1/(s1 s2) gives both 1/s1 and 1/s2.
+__device__ __forceinline__ float series_invF(float u) {
+  return 1.0f + u * (-1.0f / 3.0f + u * (-4.0f / 45.0f + u * (-44.0f / 945.0f + u * (-428.0f / 14175.0f
+             + u * (-10196.0f / 467775.0f)))));
+}
+__device__ __forceinline__ void logmean_pair(float a1, float b1, float a2, float b2, float& L1, float& iL2) {
+  const float s1 = a1 + b1, d1 = a1 - b1, s2 = a2 + b2, d2 = a2 - b2;
+  const float r = fast_rcp(s1 * s2);
+  const float rs1 = s2 * r, rs2 = s1 * r;
+  const float f1 = d1 * rs1, f2 = d2 * rs2;
+  const float u1 = f1 * f1, u2 = f2 * f2;
+  if (fmaxf(u1, u2) < LogMeanEps<float>::v) {
+    L1 = 0.5f * s1 * series_invF(u1);
+    iL2 = 2.0f * series_F(u2) * rs2;
+  } else {
+    logmean_pair_general(a1, b1, a2, b2, L1, iL2);
+  }
+}
+
 // Exact float <-> double conversions with integer instructions only (the FP64
 // pipe of this GPU is narrow and also executes the hardware conversions, and a
 // predicated hardware fallback would still occupy it).  Values below the

@@ -14,8 +14,15 @@
 //    pair data and the whole x-direction flux differencing stay in
 //    registers; only the y (and z) lines go through shared memory;
 //  * residuals of earlier stages that later stages still need (dense
-//    tableaux, N >= 4) stay in the owner's registers.
+//    tableaux, N >= 4) stay with the owner thread;
+//  * 2D Euler in FP32 (N <= 3): the thread's x-line and y-line are
+//    flux-differenced together, one in each half of packed FP32x2
+//    instructions (crkfr_f2.cuh), which halves the instructions of the pair
+//    fluxes.
 #pragma once
+#include <type_traits>
+
+#include "crkfr_f2.cuh"
 #include "crkfr_kernels.cuh"
 
 namespace crk {
@@ -85,6 +92,75 @@ __device__ __forceinline__ void line_residual(const R (&q)[N + 1][EQ::P], R (&ac
     for (int v = 0; v < M; ++v) acc[k][v] *= inv_dx;
 }
 
+// The x-line and the y-line of one thread in the two halves of packed FP32
+// pairs (2D Euler, FP32 form).  Both lines are flux-differenced in a frame
+// rotated to the line: the y half holds (rho, v_y, v_x, p, aux), so the
+// normal direction is the first velocity component in both halves, and the
+// momentum results of the y half come out in (normal, tangential) order.
+template <class EQ>
+struct PackXY {
+  static constexpr bool value = EQ::DIM == 2 && !EQ::NC;
+  // pair-data / residual component of the x line -> of the y half
+  __host__ __device__ static constexpr int rot(int c) { return c == 1 ? 2 : (c == 2 ? 1 : c); }
+};
+
+template <class EQ, int N>
+__device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2 (&acc)[N + 1][EQ::M],
+                                                 f2 (&fend)[2][EQ::M], const PhysParams<f2>& pp,
+                                                 const RefTab<float>& tb, f2 inv_dx) {
+  constexpr int n = N + 1, M = EQ::M;
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < M; ++v) acc[k][v] = f2(0.0f);
+#pragma unroll
+  for (int a = 0; a < n; ++a)
+#pragma unroll
+    for (int b = a + 1; b < n; ++b) {
+      f2 f[M];
+      EQ::two_point(0, q[a], q[b], f, pp);
+      const f2 dab(2.0f * tb.D[a][b]), dba(2.0f * tb.D[b][a]);
+#pragma unroll
+      for (int v = 0; v < M; ++v) { acc[a][v] += dab * f[v]; acc[b][v] += dba * f[v]; }
+    }
+  // end points last: the fluxes there stay live only until the face sums
+  EQ::flux(0, q[0], fend[0], pp);
+  EQ::flux(0, q[N], fend[1], pp);
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    acc[0][v] += f2(2.0f * tb.D[0][0]) * fend[0][v];
+    acc[N][v] += f2(2.0f * tb.D[N][N]) * fend[1][v];
+  }
+#pragma unroll
+  for (int k = 0; k < n; ++k)
+#pragma unroll
+    for (int v = 0; v < M; ++v) acc[k][v] *= inv_dx;
+}
+
+
+// Time averages at the two end points of one line in direction D (the face
+// nodes of the two faces normal to D): U = sum_i b_i u^(i), F^D = sum_i b_i
+// f^D(u^(i)) (eq. disc.avg.flux), lambda_D(u^n), and for the non-conservative
+// system F^nc,D = sum_i b_i B^D g^D (Sec. 2.3).  One record per end.
+template <class EQ, typename R, bool NC = EQ::NC>
+struct FaceAccNc {
+  R Nc[2][EQ::M];
+};
+template <class EQ, typename R>
+struct FaceAccNc<EQ, R, false> {};
+
+template <class EQ, typename R>
+struct FaceAcc : FaceAccNc<EQ, R> {
+  static constexpr int M = EQ::M;
+  R U[2][M], F[2][M], lam[2];
+};
+
+// Register budget of the 2D Euler lane kernels of degree 4 and 5 (resident
+// CTAs per SM; measured: more CTAs outweigh the spills up to the shared-memory
+// limit) and the highest degree that takes the packed x/y form (above it both
+// lines' pair data no longer fit in the budget).
+constexpr int kMinB4 = 3, kMinB5 = 2, kPackMaxN = 3;
+
 template <class EQ, int N, typename R>
 struct LaneLayout {
   static constexpr int DIM = EQ::DIM, M = EQ::M, P = EQ::P, n = N + 1;
@@ -97,20 +173,13 @@ struct LaneLayout {
   static constexpr int EPB = 32;
   static constexpr int THREADS = 32 * NF;
   static constexpr size_t bytes() { return sizeof(R) * (size_t)SZ * EPB; }
-  // CTAs per SM the register allocation aims at
-  static constexpr int MINB = (!EQ::NC && THREADS <= 128) ? 4 : 1;
+  // packed x/y form (2D Euler, FP32 pair fluxes)
+  static constexpr bool PACK = PackXY<EQ>::value && sizeof(R) == 4 && N <= kPackMaxN;
+  // CTAs per SM the register allocation aims at (the packed form holds both
+  // lines' pair data at once)
+  static constexpr int MINB = (!EQ::NC && THREADS <= 128) ? (PACK ? 3 : 4)
+                            : (DIM == 2 && !EQ::NC) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
-};
-
-// Time averages at the two end points of one line in direction D (the face
-// nodes of the two faces normal to D): U = sum_i b_i u^(i), F^D = sum_i b_i
-// f^D(u^(i)) (eq. disc.avg.flux), lambda_D(u^n), and for the non-conservative
-// system F^nc,D = sum_i b_i B^D g^D (Sec. 2.3).  One record per end.
-template <class EQ, typename R>
-struct FaceAcc {
-  static constexpr int M = EQ::M;
-  R U[2][M], F[2][M], lam[2];
-  R Nc[EQ::NC ? 2 : 1][M];
 };
 
 template <class EQ, int N, typename R, int D>
@@ -222,6 +291,8 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   const int nel = (int)min(32LL, E - e0);
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
+  constexpr bool PACK = L::PACK;
+  const PhysParams<f2> pp2{f2(float(pp.gamma)), f2(float(pp.inv_gm1)), f2(float(pp.c_h)), pp.vol};
 
   R dtR;
   if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
@@ -287,11 +358,48 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         }
       }
       // ---------------- x-direction flux differencing, all in registers
-      R fend[2][M];
-      line_residual<EQ, N, R, 0>(q, ax, fend, pp, tb, inv_dx_of<R>(ma, 0));
-      face_accumulate<EQ, N, R, 0>(fx, q, fend, bi, i == 0, pp);
+      // (packed form: together with the y-line below)
+      if constexpr (!PACK) {
+        R fend[2][M];
+        line_residual<EQ, N, R, 0>(q, ax, fend, pp, tb, inv_dx_of<R>(ma, 0));
+        face_accumulate<EQ, N, R, 0>(fx, q, fend, bi, i == 0, pp);
+      }
     }
-    if (DIM > 1) {
+    if constexpr (PACK) {
+      __syncthreads();   // Q of this stage visible; RY of the last stage consumed
+      if (active) {
+        // y-line l: nodes (i = l, j = 0..N); x-line in the low halves, y-line in the high halves
+        R qy[n][P];
+        f2 q2[n][P], acc2[n][M], fe2[2][M];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int c = 0; c < P; ++c) qy[k][c] = my[L::O_Q + c * NP + l + k * n];
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int c = 0; c < P; ++c) q2[k][c] = f2(q[k][c], qy[k][PackXY<EQ>::rot(c)]);
+        line_residual_xy<EQ, N>(q2, acc2, fe2, pp2, tb, f2(inv_dx_of<float>(ma, 0), inv_dx_of<float>(ma, 1)));
+        R fex[2][M], fey[2][M];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            fex[sd][v] = fe2[sd][v].v.x;
+            fey[sd][v] = fe2[sd][PackXY<EQ>::rot(v)].v.y;
+          }
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            ax[k][v] = acc2[k][v].v.x;
+            my[L::O_RY + v * NP + l + k * n] = acc2[k][PackXY<EQ>::rot(v)].v.y;
+          }
+        face_accumulate<EQ, N, R, 0>(fx, q, fex, bi, i == 0, pp);
+        face_accumulate<EQ, N, R, 1>(fy, qy, fey, bi, i == 0, pp);
+      }
+      __syncthreads();   // RY complete
+    } else if (DIM > 1) {
       __syncthreads();   // Q of this stage visible; RY of the last stage consumed
       if (active) {
         // y-line l: nodes (i = l % n, j = 0..N, k = l / n)

@@ -30,8 +30,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 
 # sources whose code ends up in the lane-form volume and face kernels
-KERNEL_SOURCES = ("crkfr_physics.cuh", "crkfr_kernels.cuh", "crkfr_async.cuh", "crkfr_volume_lanes.cuh",
-                  "cr_variant.cuh")
+KERNEL_SOURCES = ("crkfr_physics.cuh", "crkfr_f2.cuh", "crkfr_kernels.cuh", "crkfr_async.cuh",
+                  "crkfr_volume_lanes.cuh", "cr_variant.cuh")
 
 
 def kernel_source_hash():
