@@ -91,6 +91,16 @@ struct Variant {
     return cudaGetLastError();
   }
   static cudaError_t set_smem(size_t bytes) {
+    if constexpr (kFaceLanes) {
+      cudaError_t e = cudaFuncSetAttribute(k_face_update_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FL::bytes());
+      if (e != cudaSuccess) return e;
+      if constexpr (kBatched) {
+        e = cudaFuncSetAttribute(k_face_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FL::bytes());
+        if (e != cudaSuccess) return e;
+      }
+    }
     if constexpr (kLanes) {
       if constexpr (kBatched) {
         cudaError_t e = cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -112,7 +122,7 @@ struct Variant {
   }
   static cudaError_t face_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
-      k_face_batched<EQ, N, R><<<b.grid, FL::THREADS, 0, s>>>(b.solves, b.tiles, b.ntiles, PPB<R>::get(b),
+      k_face_batched<EQ, N, R><<<b.grid, FL::THREADS, FL::bytes(), s>>>(b.solves, b.tiles, b.ntiles, PPB<R>::get(b),
                                                               PPB<R>::tab(b));
       return cudaGetLastError();
     }
@@ -125,7 +135,7 @@ struct Variant {
         cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batched<EQ, N, R>, LL::THREADS, PL::bytes());
       } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_face_batched<EQ, N, R>, FL::THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_face_batched<EQ, N, R>, FL::THREADS, FL::bytes());
       }
     }
     return nb;
@@ -139,7 +149,7 @@ struct Variant {
     o->M = EQ::M;
     o->NP = L::NP;
     o->NF = L::NF;
-    o->C = trace_stride<EQ, R>();
+    o->C = trace_comps<EQ>();
     o->dim = EQ::DIM;
     o->vol_bytes_per_elem = L::bytes_per_elem();
     o->lanes = kLanes;

@@ -21,8 +21,9 @@
 // Layouts in HBM:
 //   u     [M][E][NP] FP64        state, updated in place by k_face_update
 //   rbar  [M][E][NP] R           sum_i b_i R(u^(i))
-//   trace [DIM][2][NF][E][CP] R  face data; side 0 = xi_d = 0 face, side 1 = xi_d = 1;
-//         one record of CP values per face node (C used, padded to 16 bytes):
+//   trace [DIM][2][NF][C][E] R   face data; side 0 = xi_d = 0 face, side 1 = xi_d = 1;
+//         per face node C components, each contiguous over the elements
+//         (a warp's 32 consecutive elements load one 128-byte line):
 //         U (M), F^d (M), lambda_d(u^n) (1) [+ GLM-MHD: F^nc,d (M), u^n (M)]
 #pragma once
 #include "crkfr_async.cuh"
@@ -91,10 +92,10 @@ constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
 
 template <class EQ>
 __host__ __device__ constexpr int trace_comps() { return EQ::NC ? 4 * EQ::M + 1 : 2 * EQ::M + 1; }
-// record length in the trace array: C padded to a multiple of 16 bytes
-template <class EQ, typename R>
-__host__ __device__ constexpr int trace_stride() {
-  return (trace_comps<EQ>() + (int)(16 / sizeof(R)) - 1) / (int)(16 / sizeof(R)) * (int)(16 / sizeof(R));
+// component c of the record of face node f of face (d, side) of element e
+template <class EQ, int NF>
+__host__ __device__ __forceinline__ size_t trace_index(int d, int side, int f, int c, long long E, long long e) {
+  return ((((size_t)(d * 2 + side) * NF + f) * trace_comps<EQ>() + c) * (size_t)E) + (size_t)e;
 }
 
 template <class EQ, int N, typename R>
@@ -111,38 +112,6 @@ struct VolLayout {
   static constexpr int SZ = O_LAM + DIM * NP;    // elements of R per mesh element
   static constexpr size_t bytes_per_elem() { return sizeof(R) * (size_t)SZ; }
 };
-
-// one face record (CP values, 16-byte aligned) by vector loads / stores
-template <typename R, int CP>
-__device__ __forceinline__ void load_record(const R* __restrict__ src, R (&out)[CP]) {
-  if constexpr (sizeof(R) == 4) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-    for (int k = 0; k < CP / 4; ++k) {
-      float4 t = s4[k];
-      out[4 * k] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
-    }
-  } else {
-    const double2* s2 = reinterpret_cast<const double2*>(src);
-#pragma unroll
-    for (int k = 0; k < CP / 2; ++k) {
-      double2 t = s2[k];
-      out[2 * k] = t.x; out[2 * k + 1] = t.y;
-    }
-  }
-}
-template <typename R, int CP>
-__device__ __forceinline__ void store_record(R* __restrict__ dst, const R (&in)[CP]) {
-  if constexpr (sizeof(R) == 4) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int k = 0; k < CP / 4; ++k) d4[k] = make_float4(in[4 * k], in[4 * k + 1], in[4 * k + 2], in[4 * k + 3]);
-  } else {
-    double2* d2 = reinterpret_cast<double2*>(dst);
-#pragma unroll
-    for (int k = 0; k < CP / 2; ++k) d2[k] = make_double2(in[2 * k], in[2 * k + 1]);
-  }
-}
 
 // node index of the first node of line l in direction d, and its stride
 template <int n>
@@ -352,14 +321,13 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
         if (rk_b(N, i) != 0.0) s += R(rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
       rbar[((size_t)v * E + e0) * NP + r] = s;
     }
-  // face traces: per face node one record of C values (coalesced over c, f, elements)
-  constexpr int CP = trace_stride<EQ, R>();
+  // face traces: per face node C components (coalesced over the elements)
 #pragma unroll 1
   for (int ds = 0; ds < DIM * 2; ++ds)
     for (int idx = tid; idx < nel * NF * C; idx += NT) {
-    const int c = idx % C;
-    const int f = (idx / C) % NF;
-    const int ee = idx / (C * NF);
+    const int ee = idx % nel;
+    const int c = (idx / nel) % C;
+    const int f = idx / (nel * C);
     const int side = ds & 1;
     const int d = ds >> 1;
     const int stride = ipow(n, d);
@@ -371,7 +339,7 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
     else if (c == 2 * M) val = mm[L::O_LAM + d * NP + p];
     else if (c < 3 * M + 1) val = mm[L::O_FN + (d * M + (c - 2 * M - 1)) * NP + p];
     else val = mm[L::O_U0 + (c - 3 * M - 1) * NP + p];
-    trace[((((size_t)(d * 2 + side) * NF + f) * E) + e0 + ee) * CP + c] = val;
+    trace[trace_index<EQ, NF>(d, side, f, c, E, e0 + ee)] = val;
   }
 }
 
@@ -480,11 +448,16 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
                                           long long e_oth, int f, R* J, const PhysParams<R>& pp) {
-  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, CP = trace_stride<EQ, R>();
+  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, C = trace_comps<EQ>();
   const int side_oth = 1 - side_own;
-  R o[CP], x[CP];
-  load_record<R, CP>(trace + ((((size_t)(d * 2 + side_own) * NF + f) * E) + e_own) * CP, o);
-  load_record<R, CP>(trace + ((((size_t)(d * 2 + side_oth) * NF + f) * E) + e_oth) * CP, x);
+  R o[C], x[C];
+  const R* po = trace + trace_index<EQ, NF>(d, side_own, f, 0, E, e_own);
+  const R* px = trace + trace_index<EQ, NF>(d, side_oth, f, 0, E, e_oth);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    o[c] = po[(size_t)c * E];
+    x[c] = px[(size_t)c * E];
+  }
   const R lam = fmax(o[2 * M], x[2 * M]);
   // own is the '-' state when it is the xi = 1 side: U+ - U- = sgn (Ux - Uo)
   const R sgn = side_own == 1 ? R(1) : R(-1);

@@ -221,33 +221,30 @@ __device__ __forceinline__ void face_accumulate(FaceAcc<EQ, R>& fa, const R (&q)
   }
 }
 
-// Record of one face node: U, F, lambda [, F^nc, u^n], padded to CP.  u^n of
-// the two end nodes (non-conservative system) is read from shared memory:
-// un0 / unN point at variable 0 of the end nodes, variables NP apart.
-template <class EQ, typename R>
-__device__ __forceinline__ void write_records(R* __restrict__ trace, const FaceAcc<EQ, R>& fa, int d, int NFv,
-                                              long long E, long long e, int f, const R* un0, const R* unN,
-                                              int NPv) {
-  constexpr int M = EQ::M, C = trace_comps<EQ>(), CP = trace_stride<EQ, R>();
+// Record of one face node: U, F, lambda [, F^nc, u^n] (C components, each
+// store coalesced over the warp's elements).  u^n of the two end nodes
+// (non-conservative system) is read from shared memory: un0 / unN point at
+// variable 0 of the end nodes, variables NP apart.
+template <class EQ, typename R, int NF>
+__device__ __forceinline__ void write_records(R* __restrict__ trace, const FaceAcc<EQ, R>& fa, int d, long long E,
+                                              long long e, int f, const R* un0, const R* unN, int NPv) {
+  constexpr int M = EQ::M;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    R rec[CP];
+    R* dst = trace + trace_index<EQ, NF>(d, side, f, 0, E, e);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-      rec[v] = fa.U[side][v];
-      rec[M + v] = fa.F[side][v];
+      dst[(size_t)v * E] = fa.U[side][v];
+      dst[(size_t)(M + v) * E] = fa.F[side][v];
     }
-    rec[2 * M] = fa.lam[side];
+    dst[(size_t)(2 * M) * E] = fa.lam[side];
     if constexpr (EQ::NC) {
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        rec[2 * M + 1 + v] = fa.Nc[side][v];
-        rec[3 * M + 1 + v] = (side ? unN : un0)[v * NPv];
+        dst[(size_t)(2 * M + 1 + v) * E] = fa.Nc[side][v];
+        dst[(size_t)(3 * M + 1 + v) * E] = (side ? unN : un0)[v * NPv];
       }
     }
-#pragma unroll
-    for (int c = C; c < CP; ++c) rec[c] = R(0);
-    store_record<R, CP>(trace + ((((size_t)(d * 2 + side) * NFv + f) * E) + e) * CP, rec);
   }
 }
 
@@ -458,16 +455,16 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     const int ee = r / NP, p = r % NP;
     if (v < M && ee < nel) rbar[((size_t)v * E + e0) * NP + r] = sm[(size_t)ee * L::SZ + L::O_Q + v * NP + p];
   }
-  // ---- face records [DIM][2][NF][E][CP]: this thread owns the two ends of its
+  // ---- face records [DIM][2][NF][C][E]: this thread owns the two ends of its
   // x-, y- and z-line, i.e. face node f = l of every face; consecutive lanes
   // write consecutive records
   if (active) {
     const R* u0 = my + L::O_U0;
     // end nodes: x-line l (l n, l n + N), y-line l (by, by + N n), z-line l (l, l + N n^2)
     const int by = (l % n) + (l / n) * n * n;
-    write_records<EQ, R>(trace, fx, 0, NF, E, e0 + el, l, u0 + l * n, u0 + l * n + N, NP);
-    if (DIM > 1) write_records<EQ, R>(trace, fy, 1, NF, E, e0 + el, l, u0 + by, u0 + by + N * n, NP);
-    if (DIM > 2) write_records<EQ, R>(trace, fz, 2, NF, E, e0 + el, l, u0 + l, u0 + l + N * n * n, NP);
+    write_records<EQ, R, NF>(trace, fx, 0, E, e0 + el, l, u0 + l * n, u0 + l * n + N, NP);
+    if (DIM > 1) write_records<EQ, R, NF>(trace, fy, 1, E, e0 + el, l, u0 + by, u0 + by + N * n, NP);
+    if (DIM > 2) write_records<EQ, R, NF>(trace, fz, 2, E, e0 + el, l, u0 + l, u0 + l + N * n * n, NP);
   }
 }
 
@@ -530,7 +527,7 @@ namespace crk {
 // ---------------------------------------------------------------------------
 // Face + update kernel, lane form: 32 elements per CTA, warp = x-line index,
 // lane = element.  Every face record a warp loads (own and neighbour) is a run
-// of 32 consecutive records of the [DIM][2][NF][E][CP] trace array, and face
+// of 32 consecutive elements of the [DIM][2][NF][C][E] trace array, and face
 // membership is uniform across the warp.  u^n (FP64) and Rbar are staged
 // through shared memory with coalesced loads; u^{n+1} leaves the same way.
 // ---------------------------------------------------------------------------
@@ -539,8 +536,10 @@ struct FaceLaneLayout {
   static constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1;
   static constexpr int NP = ipow(n, DIM), NF = NP / n;
   static constexpr int THREADS = 32 * NF;
-  static constexpr size_t bytes() { return 0; }
-  static constexpr bool fits() { return THREADS <= 1024; }
+  // jumps of the faces normal to y (and z): [DIM-1][side][face node][M][32 elements]
+  static constexpr int NJ = (DIM - 1) * 2 * NF;
+  static constexpr size_t bytes() { return sizeof(R) * (size_t)NJ * M * 32; }
+  static constexpr bool fits() { return THREADS <= 1024 && bytes() <= 227 * 1024; }
 };
 
 // n contiguous values starting at src (vector loads where the alignment allows)
@@ -574,39 +573,68 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
   }
 }
 
-// One tile of 32 elements starting at e0; total_warps = warps of all tiles of
-// this solve in the launch (for the barrier-free CFL reduction).
+// One tile of 32 elements starting at e0 (sj: the CTA's shared memory);
+// total_warps = warps of all tiles of this solve in the launch (for the
+// barrier-free CFL reduction).
+//
+// Phase A: every warp computes the Rusanov jumps of 2 DIM face nodes of each
+// of its 32 elements: the two x-face nodes at the ends of its own x-line, and
+// face node f = l of both faces normal to y (and z), whatever x-line they lie
+// on, into shared memory -- the same record loads for every warp.
+// Phase B: each thread forms the increment of its x-line (eq.
+// crkfr.non.cons.final), the CFL reduction runs, and u^{n+1} is stored last,
+// so that the reduction's memory fence does not wait for the stores.
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
-                                                unsigned e0, unsigned total_warps) {
+                                                unsigned e0, unsigned total_warps, R* __restrict__ sj) {
   using L = FaceLaneLayout<EQ, N, R>;
-  constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP;
+  constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
   constexpr bool F32 = sizeof(R) == 4;
   const int tid = threadIdx.x;
   const int l = tid >> 5, el = tid & 31;
   const long long E = ma.E;
   const bool active = (long long)e0 + el < E;
+  const unsigned e = e0 + el;
+  R dtR;
+  if constexpr (F32) dtR = st->dt_next_f;
+  else dtR = st->dt_next;
 
-  R lam = R(0);
-  bool bad = false;
+  // own x-line: Rbar and u^n (N+1 contiguous values per variable), loads issued first
+  R rb[M][n];
+  double un[M][n];
+  unsigned ec[3] = {0, 0, 0};
+  R Jm[M], Jp[M];
   if (active) {
-    const unsigned e = e0 + el;
-    R dtR;
-    if constexpr (F32) dtR = st->dt_next_f;
-    else dtR = st->dt_next;
-    // own x-line: Rbar and u^n (N+1 contiguous values per variable)
-    R rb[M][n];
-    double un[M][n];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       const size_t g = ((size_t)v * E + e) * NP + l * n;
       load_line<n>(rbar + g, rb[v]);
       load_line<n>(u + g, un[v]);
     }
-    unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);
+    // ---- phase A: x faces at the own line's ends, face node l of the y / z faces
+    face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp);
+    face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp);
+#pragma unroll
+    for (int d = 1; d < DIM; ++d)
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        R J[M];
+        face_jump<EQ, N, R>(trace, E, d, side, e, neighbour_of(e, ec, d, side ? +1 : -1, ma), l, J, pp);
+        const R sc = side ? -(dtR * tb.iwN * inv_dx_of<R>(ma, d)) : dtR * tb.iw0 * inv_dx_of<R>(ma, d);
+        R* dst = sj + ((size_t)(((d - 1) * 2 + side) * NF + l) * M) * 32 + el;
+#pragma unroll
+        for (int v = 0; v < M; ++v) dst[v * 32] = sc * J[v];
+      }
+  }
+  if (DIM > 1) __syncthreads();
+
+  // ---- phase B: increment of the own x-line, new state, CFL reduction, store
+  R lam = R(0);
+  bool bad = false;
+  if (active) {
     const int cy = DIM >= 2 ? l % n : 0;
     const int cz = DIM == 3 ? l / n : 0;
     R du[n][M];
@@ -614,30 +642,24 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int v = 0; v < M; ++v) du[k][v] = -dtR * rb[v][k];
-    // x faces at the line ends (eq. crkfr.non.cons.final: - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx)
     {
-      R Jm[M], Jp[M];
-      face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp);
-      face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp);
+      // - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx at the x faces
       const R sR = dtR * tb.iwN * inv_dx_of<R>(ma, 0), sL = dtR * tb.iw0 * inv_dx_of<R>(ma, 0);
 #pragma unroll
       for (int v = 0; v < M; ++v) { du[N][v] -= sR * Jm[v]; du[0][v] += sL * Jp[v]; }
     }
-    // y / z faces: whole lines on the face (warp-uniform)
+    // y / z faces: whole lines on the face (warp-uniform), scaled jumps from phase A
 #pragma unroll
     for (int d = 1; d < DIM; ++d) {
       const int cd = d == 1 ? cy : cz;
       if (cd == 0 || cd == N) {
         const int side = cd == N ? 1 : 0;
-        const unsigned nb = neighbour_of(e, ec, d, side ? +1 : -1, ma);
-        const R s = side ? -(dtR * tb.iwN * inv_dx_of<R>(ma, d)) : dtR * tb.iw0 * inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int k = 0; k < n; ++k) {
           const int f = d == 1 ? (k + n * cz) : (k + n * cy);
-          R J[M];
-          face_jump<EQ, N, R>(trace, E, d, side, e, nb, f, J, pp);
+          const R* src = sj + ((size_t)(((d - 1) * 2 + side) * NF + f) * M) * 32 + el;
 #pragma unroll
-          for (int v = 0; v < M; ++v) du[k][v] += s * J[v];
+          for (int v = 0; v < M; ++v) du[k][v] += src[v * 32];
         }
       }
     }
@@ -655,10 +677,12 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
       bad = bad || !physical_state<EQ, R>(uu, ma, lk);
       lam = fmax(lam, lk);
     }
+  }
+  finalize_warps<R>(lam, bad, st, total_warps, true, ma.cfl, ma.dt_fixed);
+  if (active) {
 #pragma unroll
     for (int v = 0; v < M; ++v) store_line<n>(u + ((size_t)v * E + e) * NP + l * n, un[v]);
   }
-  finalize_warps<R>(lam, bad, st, total_warps, true, ma.cfl, ma.dt_fixed);
 }
 
 template <class EQ, int N, typename R>
@@ -666,8 +690,9 @@ __global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
 k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
                     DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
                     const PhysParams<R> pp, const RefTab<R> tb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u,
-                            gridDim.x * (FaceLaneLayout<EQ, N, R>::THREADS / 32));
+                            gridDim.x * (FaceLaneLayout<EQ, N, R>::THREADS / 32), reinterpret_cast<R*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -745,11 +770,14 @@ __global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
 k_face_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
                const PhysParams<R> pp, const RefTab<R> tb) {
   constexpr unsigned WPT = FaceLaneLayout<EQ, N, R>::THREADS / 32;   // warps per tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const BatchTile t = tiles[it];
     const MeshArgs ma = solves[t.solve].ma;
     face_lanes_tile<EQ, N, R>(solves[t.solve].u, (const R*)solves[t.solve].rbar, (const R*)solves[t.solve].trace,
-                              solves[t.solve].st, ma, pp, tb, t.e0, solves[t.solve].ntiles * WPT);
+                              solves[t.solve].st, ma, pp, tb, t.e0, solves[t.solve].ntiles * WPT,
+                              reinterpret_cast<R*>(smem_raw));
+    if (EQ::DIM > 1) __syncthreads();   // the jump buffer is reused by the next tile
   }
 }
 
