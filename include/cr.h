@@ -92,7 +92,7 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  *                prec and vol for all solves (and the same gamma per degree).
  *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
  * The library allocates and owns all device buffers (state, stage/trace
- * scratch, reduction partials).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+ * scratch, step records).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
 /* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */

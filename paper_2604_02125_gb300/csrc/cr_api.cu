@@ -206,10 +206,12 @@ struct cr_ctx {
   LaunchCtx lc{};
   long long E = 0, NP = 0;
   int M = 0;
-  size_t partial_blocks = 0, totals_blocks = 0;
+  size_t totals_blocks = 0;
   bool has_state = false;
+  int parity = 0;     // slot of the CFL reduction of the current state
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+  // graphs of 1 and 16 steps, one per starting parity
+  cudaGraphExec_t g1[2] = {nullptr, nullptr}, g16[2] = {nullptr, nullptr};
   // batched form
   BatchedCtx* batched = nullptr;
 };
@@ -249,30 +251,33 @@ static bool desc_valid(const cr_mesh_desc& d) {
 }
 
 static void free_single(cr_ctx* c) {
-  if (c->g1) cudaGraphExecDestroy(c->g1);
-  if (c->g16) cudaGraphExecDestroy(c->g16);
+  for (int p = 0; p < 2; ++p) {
+    if (c->g1[p]) cudaGraphExecDestroy(c->g1[p]);
+    if (c->g16[p]) cudaGraphExecDestroy(c->g16[p]);
+    c->g1[p] = c->g16[p] = nullptr;
+  }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->lc.u);
   cudaFree(c->lc.rbar);
   cudaFree(c->lc.trace);
   cudaFree(c->lc.st);
-  cudaFree(c->lc.partials);
   cudaFree(c->lc.totals_part);
-  c->g1 = c->g16 = nullptr;
   c->cap_stream = nullptr;
 }
 
-static int launch_step(cr_ctx* c, cudaStream_t s) {
+// one step from the state whose CFL reduction sits in slot `parity`
+static int launch_step(cr_ctx* c, cudaStream_t s, int parity) {
+  c->lc.slot = parity;
   CR_TRY(c->ops.volume(c->lc, s));
   CR_TRY(c->ops.face_update(c->lc, s));
   return CR_OK;
 }
 
-static int capture(cr_ctx* c, int steps, cudaGraphExec_t* out) {
+static int capture(cr_ctx* c, int steps, int parity, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CR_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   int rc = CR_OK;
-  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(c, c->cap_stream);
+  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(c, c->cap_stream, (parity + k) & 1);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (rc != CR_OK) { if (g) cudaGraphDestroy(g); return rc; }
   if (e != cudaSuccess) return cuda_status(e);
@@ -294,9 +299,8 @@ static int init_single(cr_ctx* c) {
   fill_launch_ctx(d, o, &lc);
   const long long nodes = E * o.NP;
   const long long NFt = E * o.NF;
-  // one reduction partial per CTA of the widest grid (256 nodes or 32 elements per CTA)
-  c->partial_blocks = (size_t)std::max((nodes + 255) / 256, (E + 31) / 32);
-  c->totals_blocks = c->partial_blocks;
+  // one partial sum per CTA of the totals kernel (256 nodes per CTA)
+  c->totals_blocks = (size_t)((nodes + 255) / 256);
   int rc = CR_OK;
   auto al = [&](void** p, size_t bytes) {
     if (rc != CR_OK) return;
@@ -307,7 +311,6 @@ static int init_single(cr_ctx* c) {
   al(&lc.rbar, o.real_bytes * (size_t)o.M * nodes);
   al(&lc.trace, o.real_bytes * (size_t)o.dim * 2 * o.C * NFt);
   al((void**)&lc.st, sizeof(DevState));
-  al((void**)&lc.partials, sizeof(double) * c->partial_blocks);
   al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
   if (rc != CR_OK) { free_single(c); return rc; }
   lc.ma.tma_ok = tma_ok_for(lc.u, E, o.NP);
@@ -316,8 +319,10 @@ static int init_single(cr_ctx* c) {
   CR_TRY(cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream));
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
-  rc = capture(c, 1, &c->g1);
-  if (rc == CR_OK) rc = capture(c, 16, &c->g16);
+  for (int p = 0; p < 2 && rc == CR_OK; ++p) {
+    rc = capture(c, 1, p, &c->g1[p]);
+    if (rc == CR_OK) rc = capture(c, 16, p, &c->g16[p]);
+  }
   if (rc != CR_OK) { free_single(c); return rc; }
   return CR_OK;
 }
@@ -378,6 +383,8 @@ int cr_set_state(cr_ctx* c, int solve, const double* u, int u_on_device) {
   CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->stream));
   CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
+  c->parity = 0;
+  c->lc.slot = 0;
   CR_TRY(c->ops.lambda(c->lc, c->stream));
   int rc = read_status(c);
   c->has_state = (rc == CR_OK);
@@ -389,8 +396,11 @@ int cr_step(cr_ctx* c, int nsteps) {
   if (c->batched) return batched_step(c->batched, nsteps);
   if (!c->has_state) return CR_EINVAL;
   int k = 0;
-  for (; k + 16 <= nsteps; k += 16) CR_TRY(cudaGraphLaunch(c->g16, c->stream));
-  for (; k < nsteps; ++k) CR_TRY(cudaGraphLaunch(c->g1, c->stream));
+  for (; k + 16 <= nsteps; k += 16) CR_TRY(cudaGraphLaunch(c->g16[c->parity], c->stream));   // parity unchanged
+  for (; k < nsteps; ++k) {
+    CR_TRY(cudaGraphLaunch(c->g1[c->parity], c->stream));
+    c->parity ^= 1;
+  }
   return CR_OK;
 }
 
@@ -450,11 +460,13 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
       break;
     }
     cudaEventRecord(ev[4 * k + 0], c->stream);
+    c->lc.slot = c->parity;
     if (c->ops.volume(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
     cudaEventRecord(ev[4 * k + 1], c->stream);
     cudaEventRecord(ev[4 * k + 2], c->stream);
     if (rc == CR_OK && c->ops.face_update(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
     cudaEventRecord(ev[4 * k + 3], c->stream);
+    if (rc == CR_OK) c->parity ^= 1;
   }
   if (rc == CR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CR_ECUDA;
   double tv = 0.0, tf = 0.0;

@@ -52,13 +52,14 @@ struct BatchedCtx {
   char* rbar = nullptr;
   char* trace = nullptr;
   DevState* st = nullptr;
-  double* partials = nullptr;
   double* totals_part = nullptr;
-  size_t partial_blocks = 0, totals_blocks = 0;
+  size_t totals_blocks = 0;
   BatchSolve* d_solves = nullptr;
   std::vector<BatchGroup> groups;
   bool tuned = false;
-  cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+  int parity = 0;     // slot of the CFL reductions of the current states (all solves step together)
+  // graphs of 1 and 8 steps, one per starting parity
+  cudaGraphExec_t g1[2] = {nullptr, nullptr}, g8[2] = {nullptr, nullptr};
   std::string tuning;
 };
 
@@ -76,15 +77,16 @@ static int st_of(cudaError_t e) {
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static void free_all(BatchedCtx* b) {
-  if (b->g1) cudaGraphExecDestroy(b->g1);
-  if (b->g8) cudaGraphExecDestroy(b->g8);
+  for (int p = 0; p < 2; ++p) {
+    if (b->g1[p]) cudaGraphExecDestroy(b->g1[p]);
+    if (b->g8[p]) cudaGraphExecDestroy(b->g8[p]);
+  }
   if (b->cap) cudaStreamDestroy(b->cap);
   for (auto& g : b->groups) cudaFree(g.d_tiles);
   cudaFree(b->u);
   cudaFree(b->rbar);
   cudaFree(b->trace);
   cudaFree(b->st);
-  cudaFree(b->partials);
   cudaFree(b->totals_part);
   cudaFree(b->d_solves);
 }
@@ -125,7 +127,6 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
     b->bytes_r += a256(o.real_bytes * b->nvals[k]);
     off_t[k] = b->bytes_t;
     b->bytes_t += a256(o.real_bytes * (size_t)o.dim * 2 * o.C * (size_t)(E * o.NF));
-    b->partial_blocks = std::max(b->partial_blocks, (size_t)std::max((nodes + 255) / 256, (E + 31) / 32));
     b->totals_blocks = std::max(b->totals_blocks, (size_t)((nodes + 255) / 256));
   }
   int rc = CR_OK;
@@ -136,7 +137,6 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
   al((void**)&b->rbar, b->bytes_r);
   al((void**)&b->trace, b->bytes_t);
   al((void**)&b->st, sizeof(DevState) * n);
-  al((void**)&b->partials, sizeof(double) * b->partial_blocks);
   al((void**)&b->totals_part, sizeof(double) * b->totals_blocks * 11);
   al((void**)&b->d_solves, sizeof(BatchSolve) * n);
   if (rc != CR_OK) { free_all(b); delete b; return rc; }
@@ -147,7 +147,6 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
     lc.rbar = b->rbar + off_r[k];
     lc.trace = b->trace + off_t[k];
     lc.st = b->st + k;
-    lc.partials = b->partials;
     lc.totals_part = b->totals_part;
     lc.ma.tma_ok = tma_ok_for(lc.u, lc.ma.E, b->ops[k].NP);
     std::memset(&hs[k], 0, sizeof(BatchSolve));
@@ -223,6 +222,7 @@ int batched_set_state(BatchedCtx* b, int solve, const double* u, int on_device) 
   BT(cudaMemcpyAsync(lc.u, u, sizeof(double) * b->nvals[solve],
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
   BT(cudaMemsetAsync(lc.st, 0, sizeof(DevState), b->stream));
+  lc.slot = b->parity;
   BT(b->ops[solve].lambda(lc, b->stream));
   DevState h;
   BT(cudaMemcpyAsync(&h, lc.st, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
@@ -232,17 +232,23 @@ int batched_set_state(BatchedCtx* b, int solve, const double* u, int on_device) 
   return rc;
 }
 
-static int launch_step(BatchedCtx* b, cudaStream_t s) {
+static void set_slot(BatchedCtx* b, int parity) {
+  for (auto& g : b->groups) g.vol.slot = g.face.slot = parity;
+}
+
+// one step of every solve from the states whose CFL reductions sit in slot `parity`
+static int launch_step(BatchedCtx* b, cudaStream_t s, int parity) {
+  set_slot(b, parity);
   for (auto& g : b->groups) BT(g.ops.vol_batched(g.vol, s));
   for (auto& g : b->groups) BT(g.ops.face_batched(g.face, s));
   return CR_OK;
 }
 
-static int capture(BatchedCtx* b, int steps, cudaGraphExec_t* out) {
+static int capture(BatchedCtx* b, int steps, int parity, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   BT(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   int rc = CR_OK;
-  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(b, b->cap);
+  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(b, b->cap, (parity + k) & 1);
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (rc != CR_OK) { if (g) cudaGraphDestroy(g); return rc; }
   if (e != cudaSuccess) return st_of(e);
@@ -274,6 +280,7 @@ static int autotune(BatchedCtx* b) {
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
+  set_slot(b, b->parity);   // trials run as the next step; the snapshot is restored afterwards
   char buf[256];
   b->tuning = "{";
   int rc = CR_OK;
@@ -327,8 +334,10 @@ static int ensure_ready(BatchedCtx* b) {
     if (!b->has_state[k]) return CR_EINVAL;
   if (b->tuned) return CR_OK;
   int rc = autotune(b);
-  if (rc == CR_OK) rc = capture(b, 1, &b->g1);
-  if (rc == CR_OK) rc = capture(b, 8, &b->g8);
+  for (int p = 0; p < 2 && rc == CR_OK; ++p) {
+    rc = capture(b, 1, p, &b->g1[p]);
+    if (rc == CR_OK) rc = capture(b, 8, p, &b->g8[p]);
+  }
   if (rc == CR_OK) b->tuned = true;
   return rc;
 }
@@ -337,8 +346,11 @@ int batched_step(BatchedCtx* b, int nsteps) {
   int rc = ensure_ready(b);
   if (rc != CR_OK) return rc;
   int k = 0;
-  for (; k + 8 <= nsteps; k += 8) BT(cudaGraphLaunch(b->g8, b->stream));
-  for (; k < nsteps; ++k) BT(cudaGraphLaunch(b->g1, b->stream));
+  for (; k + 8 <= nsteps; k += 8) BT(cudaGraphLaunch(b->g8[b->parity], b->stream));   // parity unchanged
+  for (; k < nsteps; ++k) {
+    BT(cudaGraphLaunch(b->g1[b->parity], b->stream));
+    b->parity ^= 1;
+  }
   return CR_OK;
 }
 
@@ -395,6 +407,7 @@ int batched_time_kernels(BatchedCtx* b, int nsteps, void* flush, size_t bytes, d
   double tv = 0.0, tf = 0.0;
   for (int k = 0; k < nsteps && rc == CR_OK; ++k) {
     if (flush && bytes) cudaMemsetAsync(flush, k & 0xff, bytes, b->stream);
+    set_slot(b, b->parity);
     cudaEventRecord(e[0], b->stream);
     for (auto& g : b->groups)
       if (g.ops.vol_batched(g.vol, b->stream) != cudaSuccess) rc = CR_ECUDA;
@@ -408,6 +421,7 @@ int batched_time_kernels(BatchedCtx* b, int nsteps, void* flush, size_t bytes, d
     cudaEventElapsedTime(&c, e[1], e[2]);
     tv += a;
     tf += c;
+    if (rc == CR_OK) b->parity ^= 1;
   }
   for (auto& x : e) cudaEventDestroy(x);
   if (rc != CR_OK) return rc;

@@ -13,7 +13,6 @@ struct LaunchCtx {
   void* rbar;
   void* trace;
   DevState* st;
-  double* partials;
   double* totals_part;
   MeshArgs ma;
   PhysParams<double> pp64;
@@ -22,6 +21,7 @@ struct LaunchCtx {
   RefTab<float> tb32;
   int epb;            // elements per CTA of the volume kernel (tile form)
   int sms;            // multiprocessors of the device (persistent grids)
+  int slot;           // step parity: CFL-reduction slot of the state the next step starts from
 };
 
 // One launch of a batched persistent kernel (all solves of one degree).
@@ -34,10 +34,11 @@ struct BatchLaunch {
   PhysParams<float> pp32;
   RefTab<double> tb64;
   RefTab<float> tb32;
+  int slot;           // step parity (as LaunchCtx::slot)
 };
 
 struct VariantOps {
-  int M, NP, NF, C, dim;       // C: record length of a face trace (padded)
+  int M, NP, NF, C, dim;       // C: components of a face record
   size_t vol_bytes_per_elem;   // shared memory per element of the tile volume kernel
   bool lanes;                  // the lane-form volume kernel is used (32 elements per CTA)
   size_t (*vol_smem)(int epb); // dynamic shared memory of one volume CTA

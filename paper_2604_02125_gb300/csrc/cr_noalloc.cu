@@ -5,16 +5,16 @@
 // has already reserved the device, or a host loop that must not stall other
 // streams, which cudaMalloc/cudaFree can do by synchronising the device.  For
 // them this entry point runs the same volume and face/update kernels as
-// cr_step, with every scratch buffer (stage residual sums, face traces,
-// reduction partials and the step record) carved out of one file-scope
+// cr_step, with every scratch buffer (stage residual sums, face traces and
+// the step record with its CFL reduction) carved out of one file-scope
 // __device__ array of CR_NOALLOC_SCRATCH_BYTES.  The caller passes the input
 // and output states; nothing is allocated or freed.
 //
 // The array exists once per device that loads the library and lives until the
 // process exits.  All calls on a device share it and it keeps the last call's
 // contents, so calls that overlap on the GPU (on different streams, or from
-// several threads) race; the step record and the reduction ticket are cleared
-// at the start of every call.
+// several threads) race; the step record is cleared at the start of every
+// call.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -83,10 +83,8 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   long long E = 1;
   for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
   const long long nodes = E * o.NP;
-  const size_t blocks = (size_t)(((nodes + 255) / 256) > ((E + 31) / 32) ? (nodes + 255) / 256 : (E + 31) / 32);
-  // scratch layout: step record | reduction partials | rbar | face traces
-  const size_t off_part = align256(sizeof(DevState));
-  const size_t off_rbar = off_part + align256(sizeof(double) * blocks);
+  // scratch layout: step record | rbar | face traces
+  const size_t off_rbar = align256(sizeof(DevState));
   const size_t off_trace = off_rbar + align256(o.real_bytes * (size_t)o.M * nodes);
   const size_t need = off_trace + align256(o.real_bytes * (size_t)o.dim * 2 * o.C * (E * o.NF));
   if (need > (size_t)CR_NOALLOC_SCRATCH_BYTES) return CR_ETOOLARGE;
@@ -103,7 +101,6 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   memset(&lc, 0, sizeof(lc));
   lc.u = u_out;
   lc.st = (DevState*)base;
-  lc.partials = (double*)(base + off_part);
   lc.rbar = base + off_rbar;
   lc.trace = base + off_trace;
   lc.totals_part = nullptr;
@@ -133,8 +130,9 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
       (e = cudaMemcpyAsync(u_out, u_in, sizeof(double) * (size_t)o.M * nodes, cudaMemcpyDeviceToDevice, s)) !=
           cudaSuccess)
     return to_status(e);
-  // the shared step record starts clean: t, steps, status, ticket
+  // the shared step record starts clean: t, steps, status, CFL slots (slot 0: u^n)
   if ((e = cudaMemsetAsync(lc.st, 0, sizeof(DevState), s)) != cudaSuccess) return to_status(e);
+  lc.slot = 0;
   if ((e = o.lambda(lc, s)) != cudaSuccess) return to_status(e);
   if ((e = o.volume(lc, s)) != cudaSuccess) return to_status(e);
   if ((e = o.face_update(lc, s)) != cudaSuccess) return to_status(e);

@@ -52,13 +52,13 @@ struct Variant {
       const long long ntiles = (c.ma.E + 31) / 32;
       const long long grid = std::min(ntiles, (long long)c.sms * vol_occupancy());
       k_volume_lanes<EQ, N, R><<<(unsigned)grid, LL::THREADS, PL::bytes(), s>>>(
-          c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c));
+          c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot);
     } else {
       const long long grid = (c.ma.E + c.epb - 1) / c.epb;
       const int threads = c.epb * L::NF;
       const size_t smem = (size_t)c.epb * L::bytes_per_elem();
       k_volume_tile<EQ, N, R><<<(unsigned)grid, threads, smem, s>>>(c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma,
-                                                                    PP<R>::get(c), PP<R>::tab(c));
+                                                                    PP<R>::get(c), PP<R>::tab(c), c.slot);
     }
     return cudaGetLastError();
   }
@@ -69,19 +69,19 @@ struct Variant {
     if constexpr (kFaceLanes) {
       const unsigned grid = (unsigned)((c.ma.E + 31) / 32);
       k_face_update_lanes<EQ, N, R><<<grid, FL::THREADS, FL::bytes(), s>>>(
-          c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma, PP<R>::get(c), PP<R>::tab(c));
+          c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot);
     } else {
       const long long total = c.ma.E * L::NP;
       const unsigned grid = (unsigned)((total + 255) / 256);
-      k_face_update<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.partials, c.ma,
-                                                    PP<R>::get(c), PP<R>::tab(c));
+      k_face_update<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.ma,
+                                                    PP<R>::get(c), PP<R>::tab(c), c.slot);
     }
     return cudaGetLastError();
   }
   static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {
     const long long total = c.ma.E * L::NP;
     const unsigned grid = (unsigned)((total + 255) / 256);
-    k_lambda<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.st, c.partials, c.ma);
+    k_lambda<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.st, c.ma, c.slot);
     return cudaGetLastError();
   }
   static cudaError_t totals(const LaunchCtx& c, cudaStream_t s) {
@@ -115,7 +115,7 @@ struct Variant {
   static cudaError_t vol_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
       k_volume_batched<EQ, N, R><<<b.grid, LL::THREADS, PL::bytes(), s>>>(
-          b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b));
+          b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b), b.slot);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -123,7 +123,7 @@ struct Variant {
   static cudaError_t face_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
       k_face_batched<EQ, N, R><<<b.grid, FL::THREADS, FL::bytes(), s>>>(b.solves, b.tiles, b.ntiles, PPB<R>::get(b),
-                                                              PPB<R>::tab(b));
+                                                                        PPB<R>::tab(b), b.slot);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;

@@ -76,19 +76,70 @@ struct RefTab {
   signed char slot[7];   // register slot of a stage residual needed beyond the next stage, else -1
 };
 
+// Step record of one solve.  The CFL reduction needs no fence and no
+// ticket: the wave-speed maximum of a state is accumulated by fire-and-forget
+// atomics into lam_bits[slot], where slot alternates with the step parity
+// (the host passes it to every kernel); the volume kernel of the step that
+// starts from that state reads it (kernel boundaries order the two), derives
+// dt, records the step and clears the other slot for the new state.
 struct DevState {
-  double lam_max;      // max over nodes of sum_d lambda_d / dx_d of the current state
-  double dt;           // dt of the last completed step
-  double dt_next;      // dt of the next step: cfl / lam_max or dt_fixed (set by the reductions)
-  float dt_next_f;     // the same, rounded to FP32
-  double t;
+  unsigned long long lam_bits[2];   // max over nodes of sum_d lambda_d / dx_d (bits of a non-negative double)
+  double dt;           // dt of the last step (set when the step starts)
+  double t;            // time after the last step
+  double lam_max;      // wave-speed maximum the last step's dt came from
   long long steps;
   unsigned status;     // bit 0: non-physical state, bit 1: barrier timeout
-  unsigned counter;    // last-block / last-warp ticket of the reductions
-  unsigned long long lam_bits;   // running max (bits of a non-negative double) of the warp reduction
+  unsigned pad;
 };
 
 constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
+
+// ---------------------------------------------------------------------------
+// CFL reduction: every warp takes its maximum with shuffles and folds it into
+// lam_bits[slot] with one 64-bit atomicMax (non-negative doubles order like
+// their bit patterns; the result is not waited for).  Must be reached by every
+// lane of the warp.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void reduce_lambda(T lam, bool bad, DevState* st, int slot) {
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (anybad) atomicOr(&st->status, ST_NONPHYS);
+    atomicMax(&st->lam_bits[slot], (unsigned long long)__double_as_longlong((double)lam));
+  }
+}
+
+// dt of the step that starts now, from the wave-speed maximum of its initial
+// state: cfl / max_nodes sum_d lambda_d/dx_d, or the fixed dt.  Every caller
+// computes the same value; the one with lead set (one per solve and launch)
+// records the step and clears the other slot for the new state's reduction.
+__device__ __forceinline__ double step_begin(DevState* st, int slot, double cfl, double dt_fixed, bool lead) {
+  const double lam = __longlong_as_double((long long)st->lam_bits[slot]);
+  const double dt = dt_fixed > 0.0 ? dt_fixed : cfl / lam;
+  if (lead) {
+    st->lam_bits[slot ^ 1] = 0ull;
+    st->dt = dt;
+    st->t += dt;
+    st->steps += 1;
+    st->lam_max = lam;
+    if (!(lam > 0.0) || !isfinite(lam)) atomicOr(&st->status, ST_NONPHYS);
+  }
+  return dt;
+}
+
+// the current step's dt in the path's arithmetic (face kernels, after the
+// volume kernel of the same step has recorded it)
+template <typename R>
+__device__ __forceinline__ R dt_as(double dt) {
+  if constexpr (sizeof(R) == 4) return d2f_int(dt);
+  else return dt;
+}
+template <typename R>
+__device__ __forceinline__ R step_dt(const DevState* st) {
+  return dt_as<R>(st->dt);
+}
+
 
 template <class EQ>
 __host__ __device__ constexpr int trace_comps() { return EQ::NC ? 4 * EQ::M + 1 : 2 * EQ::M + 1; }
@@ -145,7 +196,7 @@ __device__ __forceinline__ unsigned neighbour_of(unsigned e, const unsigned (&c)
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
-         DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+         DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, int slot) {
   using L = VolLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
   constexpr int C = trace_comps<EQ>();
@@ -162,9 +213,10 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
   const bool active = el < nel;
   R* my = sm + (size_t)el * L::SZ;
 
-  R dtR;
-  if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
-  else dtR = st->dt_next;
+  __shared__ double s_dt;
+  if (tid == 0) s_dt = step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0);
+  __syncthreads();
+  const R dtR = dt_as<R>(s_dt);
 
   // u^n -> shared memory (coalesced over [v][e0..e0+nel)[p])
 #pragma unroll 1
@@ -343,89 +395,6 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
   }
 }
 
-// ---------------------------------------------------------------------------
-// block-wide max / or, then the last block finalises the grid reduction
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void finalize_lambda(T lam, bool bad, DevState* st, double* partials, bool advance_time,
-                                                double ma_cfl, double ma_dt_fixed) {
-  __shared__ T s_max[32];
-  __shared__ bool s_last;
-  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  unsigned anybad = __ballot_sync(0xffffffffu, bad);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_max[w] = lam;
-    if (anybad) atomicOr(&st->status, ST_NONPHYS);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    T m = T(0);
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, s_max[k]);
-    partials[blockIdx.x] = (double)m;
-    __threadfence();
-    unsigned ticket = atomicAdd(&st->counter, 1u);
-    s_last = (ticket == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    double m = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) m = fmax(m, __ldcg(&partials[k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ double s_fin[32];
-    if (lane == 0) s_fin[w] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double mm = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, s_fin[k]);
-      if (advance_time) {
-        st->dt = st->dt_next;
-        st->t += st->dt;
-        st->steps += 1;
-      }
-      st->lam_max = mm;
-      if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
-      st->dt_next = ma_dt_fixed > 0.0 ? ma_dt_fixed : ma_cfl / mm;
-      st->dt_next_f = (float)st->dt_next;
-      st->counter = 0u;
-    }
-  }
-}
-
-// Barrier-free CFL reduction: every warp takes its max with shuffles and
-// folds it into st->lam_bits with one 64-bit atomicMax (non-negative doubles
-// order like their bit patterns); the last warp to take a ticket sets
-// lam_max, the next dt and the time, and clears the accumulators.  Must be
-// reached by every lane of every warp of the grid.
-template <typename T>
-__device__ __forceinline__ void finalize_warps(T lam, bool bad, DevState* st, unsigned total_warps, bool advance_time,
-                                               double ma_cfl, double ma_dt_fixed) {
-  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  const unsigned anybad = __ballot_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    if (anybad) atomicOr(&st->status, ST_NONPHYS);
-    atomicMax(&st->lam_bits, (unsigned long long)__double_as_longlong((double)lam));
-    __threadfence();
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
-    if (ticket == total_warps - 1) {
-      __threadfence();
-      const double mm = __longlong_as_double((long long)atomicAdd(&st->lam_bits, 0ull));
-      if (advance_time) {
-        st->dt = st->dt_next;
-        st->t += st->dt;
-        st->steps += 1;
-      }
-      st->lam_max = mm;
-      if (!(mm > 0.0) || !isfinite(mm)) st->status |= ST_NONPHYS;
-      st->dt_next = ma_dt_fixed > 0.0 ? ma_dt_fixed : ma_cfl / mm;
-      st->dt_next_f = (float)st->dt_next;
-      st->lam_bits = 0ull;
-      st->counter = 0u;
-    }
-  }
-}
-
 // physicality and sum_d lambda_d/dx_d of an updated state; the FP32 form
 // evaluates the wave speeds in FP32 (the dt reduction is a max)
 template <class EQ, typename R>
@@ -481,8 +450,8 @@ __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
-              DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
-              const PhysParams<R> pp, const RefTab<R> tb) {
+              DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+              int slot) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM);
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
@@ -494,9 +463,7 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
     const int p = (int)(gid % NP);
     unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);
-    R dtR;
-    if constexpr (F32) dtR = st->dt_next_f;
-    else dtR = st->dt_next;
+    const R dtR = step_dt<R>(st);
     // increment of the final update (eq. crkfr.non.cons.final) in the path's
     // arithmetic: -dt Rbar - dt J^- g_R'(1)/dx + dt J^+ (-g_L'(0))/dx
     R du[M];
@@ -537,14 +504,14 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
     }
     bad = !physical_state<EQ, R>(uu, ma, lam);
   }
-  finalize_lambda<R>(lam, bad, st, partials, true, ma.cfl, ma.dt_fixed);
+  reduce_lambda<R>(lam, bad, st, slot ^ 1);
 }
 
 // CFL reduction of the current state (used after set_state); wave speeds in
 // the path's arithmetic R, like the reduction inside k_face_update
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
-k_lambda(const double* __restrict__ u, DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma) {
+k_lambda(const double* __restrict__ u, DevState* __restrict__ st, const MeshArgs ma, int slot) {
   constexpr int M = EQ::M, NP = ipow(N + 1, EQ::DIM);
   const long long E = ma.E;
   const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -558,7 +525,7 @@ k_lambda(const double* __restrict__ u, DevState* __restrict__ st, double* __rest
     for (int v = 0; v < M; ++v) uu[v] = u[((size_t)v * E + e) * NP + p];
     bad = !physical_state<EQ, R>(uu, ma, lam);
   }
-  finalize_lambda<R>(lam, bad, st, partials, false, ma.cfl, ma.dt_fixed);
+  reduce_lambda<R>(lam, bad, st, slot);
 }
 
 // FP64 quadrature-weighted totals: per block partial sums, fixed order

@@ -275,7 +275,7 @@ template <class EQ, int N, typename R>
 __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
                                                   R* __restrict__ trace, const DevState* __restrict__ st,
                                                   const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
-                                                  long long e0, R* sm, const double* staged = nullptr,
+                                                  long long e0, R dtR, R* sm, const double* staged = nullptr,
                                                   Prefetch pf = Prefetch{nullptr, 0, 0, nullptr, nullptr}) {
   using L = LaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
@@ -290,10 +290,6 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   R* my = sm + (size_t)el * L::SZ;
   constexpr bool PACK = L::PACK;
   const PhysParams<f2> pp2{f2(float(pp.gamma)), f2(float(pp.inv_gm1)), f2(float(pp.c_h)), pp.vol};
-
-  R dtR;
-  if constexpr (sizeof(R) == 4) dtR = st->dt_next_f;
-  else dtR = st->dt_next;
 
   // ---- u^n: coalesced into shared memory (staging in the Q region), then own x-line to registers
   // (index arithmetic with compile-time divisors only)
@@ -485,7 +481,8 @@ struct PersistLayout {
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
 k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
-               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb) {
+               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+               int slot) {
   using PL = PersistLayout<EQ, N, R>;
   constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -498,8 +495,13 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
   auto pf_of = [&](unsigned t) {
     return Prefetch{u + (size_t)t * 32 * NP, E * NP, (unsigned)(32 * NP * sizeof(double)), staging, bar};
   };
-  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __shared__ double s_dt;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    s_dt = step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0);
+  }
   __syncthreads();
+  const R dtR = dt_as<R>(s_dt);
   unsigned phase = 0;
   unsigned t = blockIdx.x;
   if (t < ntiles && whole(t) && threadIdx.x == 0) issue_prefetch<M>(pf_of(t));
@@ -515,7 +517,8 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
     }
     const unsigned tn = t + gridDim.x;
     const Prefetch pf = (tn < ntiles && whole(tn)) ? pf_of(tn) : Prefetch{nullptr, 0, 0, nullptr, nullptr};
-    volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, sm, staged ? staging : nullptr, pf);
+    volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
+                                staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }
 }
@@ -573,9 +576,8 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
   }
 }
 
-// One tile of 32 elements starting at e0 (sj: the CTA's shared memory);
-// total_warps = warps of all tiles of this solve in the launch (for the
-// barrier-free CFL reduction).
+// One tile of 32 elements starting at e0 (sj: the CTA's shared memory; slot:
+// step parity of the CFL reduction).
 //
 // Phase A: every warp computes the Rusanov jumps of 2 DIM face nodes of each
 // of its 32 elements: the two x-face nodes at the ends of its own x-line, and
@@ -583,12 +585,12 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
 // on, into shared memory -- the same record loads for every warp.
 // Phase B: each thread forms the increment of its x-line (eq.
 // crkfr.non.cons.final), the CFL reduction runs, and u^{n+1} is stored last,
-// so that the reduction's memory fence does not wait for the stores.
+// after the reduction's atomics.
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
-                                                unsigned e0, unsigned total_warps, R* __restrict__ sj) {
+                                                unsigned e0, int slot, R* __restrict__ sj) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
   constexpr bool F32 = sizeof(R) == 4;
@@ -597,9 +599,7 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   const long long E = ma.E;
   const bool active = (long long)e0 + el < E;
   const unsigned e = e0 + el;
-  R dtR;
-  if constexpr (F32) dtR = st->dt_next_f;
-  else dtR = st->dt_next;
+  const R dtR = step_dt<R>(st);
 
   // own x-line: Rbar and u^n (N+1 contiguous values per variable), loads issued first
   R rb[M][n];
@@ -678,7 +678,7 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
       lam = fmax(lam, lk);
     }
   }
-  finalize_warps<R>(lam, bad, st, total_warps, true, ma.cfl, ma.dt_fixed);
+  reduce_lambda<R>(lam, bad, st, slot ^ 1);
   if (active) {
 #pragma unroll
     for (int v = 0; v < M; ++v) store_line<n>(u + ((size_t)v * E + e) * NP + l * n, un[v]);
@@ -688,11 +688,10 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
 k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
-                    DevState* __restrict__ st, double* __restrict__ partials, const MeshArgs ma,
-                    const PhysParams<R> pp, const RefTab<R> tb) {
+                    DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                    int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u,
-                            gridDim.x * (FaceLaneLayout<EQ, N, R>::THREADS / 32), reinterpret_cast<R*>(smem_raw));
+  face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot, reinterpret_cast<R*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -718,7 +717,7 @@ struct BatchTile {
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
 k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
-                 const PhysParams<R> pp, const RefTab<R> tb) {
+                 const PhysParams<R> pp, const RefTab<R> tb, int slot) {
   using PL = PersistLayout<EQ, N, R>;
   constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -759,8 +758,12 @@ k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restr
       if (whole(tn)) pf = pf_of(tn);
     }
     const MeshArgs ma = bs.ma;
-    volume_lanes_tile<EQ, N, R>(bs.u, (R*)bs.rbar, (R*)bs.trace, bs.st, ma, pp, tb, (long long)t.e0, sm,
-                                staged ? staging : nullptr, pf);
+    // dt of this solve's step; its first tile records the step
+    __shared__ double s_dt;
+    if (threadIdx.x == 0) s_dt = step_begin(bs.st, slot, ma.cfl, ma.dt_fixed, t.e0 == 0);
+    __syncthreads();
+    volume_lanes_tile<EQ, N, R>(bs.u, (R*)bs.rbar, (R*)bs.trace, bs.st, ma, pp, tb, (long long)t.e0,
+                                dt_as<R>(s_dt), sm, staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }
 }
@@ -768,15 +771,13 @@ k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restr
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
 k_face_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
-               const PhysParams<R> pp, const RefTab<R> tb) {
-  constexpr unsigned WPT = FaceLaneLayout<EQ, N, R>::THREADS / 32;   // warps per tile
+               const PhysParams<R> pp, const RefTab<R> tb, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const BatchTile t = tiles[it];
     const MeshArgs ma = solves[t.solve].ma;
     face_lanes_tile<EQ, N, R>(solves[t.solve].u, (const R*)solves[t.solve].rbar, (const R*)solves[t.solve].trace,
-                              solves[t.solve].st, ma, pp, tb, t.e0, solves[t.solve].ntiles * WPT,
-                              reinterpret_cast<R*>(smem_raw));
+                              solves[t.solve].st, ma, pp, tb, t.e0, slot, reinterpret_cast<R*>(smem_raw));
     if (EQ::DIM > 1) __syncthreads();   // the jump buffer is reused by the next tile
   }
 }
