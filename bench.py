@@ -199,6 +199,34 @@ def run_batched(crkfr, inputs, stream, steps):
                         "densities (amplitude 0.1-0.5) and shear, FP32 pair fluxes, FP64 update"}
 
 
+# reduced meshes of every workload for single-threaded oracle timings (a few
+# seconds each); the GPU side of the same workloads is measured by
+# paper_2604_02125_gb300/measure_configs.py
+ORACLE_SAMPLES = {
+    "wave1d_64_N3": ("density_wave_1d", dict(cells=64, N=3), 2000),
+    "shear2d_256_N3": ("shear_layer_2d", dict(cells=(32, 32), N=3), 40),
+    "shear2d_256_N3_kep": ("shear_layer_2d", dict(cells=(32, 32), N=3, vol="kep"), 40),
+    "mhd2d_128_N4": ("mhd_vortex_2d", dict(cells=(16, 16), N=4), 40),
+    "tgv3d_64_N3": ("tgv_3d", dict(cells=(8, 8, 8), N=3), 20),
+}
+
+
+def cpu_baseline_configs():
+    """The FP64 oracle, single thread, on a reduced mesh of every workload."""
+    import oracle
+    from paper_2604_02125_gb300 import inputs
+    oracle.build()
+    for name, (fn, kw, steps) in ORACLE_SAMPLES.items():
+        mesh, U = getattr(inputs, fn)(**kw)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            U = oracle.step(mesh, U, oracle.cfl_dt(mesh, U))
+        el = time.perf_counter() - t0
+        nodes = inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
+        print(json.dumps({"workload": name, "kind": "oracle", "cores": 1, "dof_updates_per_s": nodes * steps / el,
+                          "sample": "%s%s, %d steps, %d nodes, %.2f s" % (fn, kw, steps, nodes, el)}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -235,7 +263,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--cpu-baseline-configs", action="store_true",
+                    help="only time the FP64 oracle on reduced meshes of every workload")
     args = ap.parse_args()
+    if args.cpu_baseline_configs:
+        return cpu_baseline_configs()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
