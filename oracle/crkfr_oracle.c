@@ -26,7 +26,7 @@
  *   - final update (eqs. crkfr.non.cons.final, total.F.non.cons) with the
  *     flux-differencing time-averaged volume term (Sec. 3).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - multi-D: tensor product, sum of per-direction 1D operators on a
  *     uniform periodic Cartesian grid;
  *   - Butcher tableaux per degree N (order N+1), see or_butcher();
@@ -575,87 +575,157 @@ static void nc_with_gavg(const or_desc *d, int dir, const double *un_side, const
   nc_product(d, dir, un_side, gavg_state, out);
 }
 
+/* Time-averaged data of a set of elements: element e sits at local index
+ * loc[e] of the W arrays (Fbar, Fnc: [dir][nloc][np][M]). */
+typedef struct {
+  or_work W;
+  int *loc;     /* [E] local index or -1 */
+  int nloc;
+} or_set;
+
+static void set_alloc(or_set *S, int E, int nloc, size_t sz, int dim) {
+  S->nloc = nloc;
+  S->loc = malloc(sizeof(int) * E);
+  for (int e = 0; e < E; ++e) S->loc[e] = -1;
+  S->W.Rbar = malloc(sizeof(double) * sz * nloc);
+  S->W.Ubar = malloc(sizeof(double) * sz * nloc);
+  S->W.Fbar = malloc(sizeof(double) * sz * nloc * dim);
+  S->W.Fnc = malloc(sizeof(double) * sz * nloc * dim);
+  S->W.un = malloc(sizeof(double) * sz * nloc);
+}
+static void set_free(or_set *S) {
+  free(S->loc); free(S->W.Rbar); free(S->W.Ubar); free(S->W.Fbar); free(S->W.Fnc); free(S->W.un);
+}
+
+/* 1. element-local stages and time averages of element e into local slot k */
+static void set_stages(const or_desc *d, const or_mesh *m, const double *Un, double dt, or_set *S, int e, int k) {
+  size_t sz = (size_t)m->np * m->M;
+  int dim = d->dim;
+  double *fb = malloc(sizeof(double) * sz * dim), *fn = malloc(sizeof(double) * sz * dim);
+  S->loc[e] = k;
+  gather_elem(m, Un, e, &S->W.un[k * sz]);
+  element_stages(d, m, &S->W.un[k * sz], dt, &S->W.Rbar[k * sz], &S->W.Ubar[k * sz], fb, fn);
+  for (int dir = 0; dir < dim; ++dir)
+    for (size_t q = 0; q < sz; ++q) {
+      S->W.Fbar[((size_t)dir * S->nloc + k) * sz + q] = fb[dir * sz + q];
+      S->W.Fnc[((size_t)dir * S->nloc + k) * sz + q] = fn[dir * sz + q];
+    }
+  free(fb);
+  free(fn);
+}
+
+/* 2. final update of element e ([node][var] into unew), with the face terms of
+ *    eq. crkfr.non.cons.final evaluated at both faces of every direction; the
+ *    element and its neighbours must be in the set. */
+static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int e, double dt, double *unew) {
+  int M = m->M, np = m->np, dim = d->dim;
+  size_t sz = (size_t)np * M;
+  const or_work *W = &S->W;
+  const int ke = S->loc[e];
+  for (size_t k = 0; k < sz; ++k) unew[k] = W->un[ke * sz + k] - dt * W->Rbar[ke * sz + k];
+  for (int dir = 0; dir < dim; ++dir) {
+    for (int side = 0; side < 2; ++side) {
+      /* side 1: interface e+1/2 (element e is the '-' state); side 0: e-1/2 (e is '+') */
+      int nb = neighbour(d, e, dir, side ? +1 : -1);
+      const int kn = S->loc[nb];
+      const double *Fe = &W->Fbar[((size_t)dir * S->nloc + ke) * sz], *Fn = &W->Fbar[((size_t)dir * S->nloc + kn) * sz];
+      const double *Ne = &W->Fnc[((size_t)dir * S->nloc + ke) * sz], *Nn = &W->Fnc[((size_t)dir * S->nloc + kn) * sz];
+      for (int fnode = 0; fnode < np; ++fnode) {
+        int fijk[3];
+        node_ijk(m, fnode, dim, fijk);
+        if (fijk[dir] != 0) continue;            /* enumerate face nodes once */
+        double um[OR_MAXM], up[OR_MAXM], Um[OR_MAXM], Up[OR_MAXM], Fm[OR_MAXM], Fp[OR_MAXM], Nm[OR_MAXM], Np_[OR_MAXM];
+        const double *uel = &W->un[ke * sz], *unb = &W->un[kn * sz];
+        const double *Uel = &W->Ubar[ke * sz], *Unb = &W->Ubar[kn * sz];
+        if (side) {   /* e is '-', nb is '+' */
+          extrapolate(d, m, uel, dir, 1, fijk, um); extrapolate(d, m, unb, dir, 0, fijk, up);
+          extrapolate(d, m, Uel, dir, 1, fijk, Um); extrapolate(d, m, Unb, dir, 0, fijk, Up);
+          extrapolate(d, m, Fe, dir, 1, fijk, Fm);  extrapolate(d, m, Fn, dir, 0, fijk, Fp);
+          extrapolate(d, m, Ne, dir, 1, fijk, Nm);  extrapolate(d, m, Nn, dir, 0, fijk, Np_);
+        } else {      /* nb is '-', e is '+' */
+          extrapolate(d, m, unb, dir, 1, fijk, um); extrapolate(d, m, uel, dir, 0, fijk, up);
+          extrapolate(d, m, Unb, dir, 1, fijk, Um); extrapolate(d, m, Uel, dir, 0, fijk, Up);
+          extrapolate(d, m, Fn, dir, 1, fijk, Fm);  extrapolate(d, m, Fe, dir, 0, fijk, Fp);
+          extrapolate(d, m, Nn, dir, 1, fijk, Nm);  extrapolate(d, m, Ne, dir, 0, fijk, Np_);
+        }
+        /* eq. numflux.cons: F^num = (F- + F+)/2 - lambda/2 (U+ - U-) */
+        double lm = wave_speed(d, dir, um), lp = wave_speed(d, dir, up);
+        double lam = lm > lp ? lm : lp;
+        double Fnum[OR_MAXM], ncs[OR_MAXM];
+        for (int v = 0; v < M; ++v) Fnum[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * lam * (Up[v] - Um[v]);
+        /* F^{num,+-}_nc = B(u^{n,+-}) g^avg(U); the jump F^num_{+-} - F^tot_{+-} */
+        double J[OR_MAXM];
+        if (side) {
+          nc_with_gavg(d, dir, um, Um, Up, ncs);
+          for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fm[v] + Nm[v]);
+        } else {
+          nc_with_gavg(d, dir, up, Um, Up, ncs);
+          for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fp[v] + Np_[v]);
+        }
+        /* - dt J d_x g_R (side 1) or - dt J d_x g_L (side 0), at every node of the line */
+        for (int p = 0; p < m->n; ++p) {
+          int ijk[3] = {fijk[0], fijk[1], fijk[2]};
+          ijk[dir] = p;
+          int id = node_id(m, ijk, dim);
+          double dg = (side ? m->dgR[p] : m->dgL[p]) / m->dx[dir];
+          for (int v = 0; v < M; ++v) unew[id * M + v] -= dt * J[v] * dg;
+        }
+      }
+    }
+  }
+}
+
 /* Exported: one cRKFR step u^n -> u^{n+1} with the given dt. */
 int or_step(const or_desc *d, const double *Un, double dt, double *Unew) {
   or_mesh m;
   if (mesh_setup(d, &m)) return -1;
-  int M = m.M, np = m.np, E = m.E, dim = d->dim;
+  int M = m.M, np = m.np, E = m.E;
   size_t sz = (size_t)np * M;
-  or_work W;
-  W.Rbar = malloc(sizeof(double) * sz * E);
-  W.Ubar = malloc(sizeof(double) * sz * E);
-  W.Fbar = malloc(sizeof(double) * sz * E * dim);
-  W.Fnc = malloc(sizeof(double) * sz * E * dim);
-  W.un = malloc(sizeof(double) * sz * E);
-  double *fb = malloc(sizeof(double) * sz * dim), *fn = malloc(sizeof(double) * sz * dim);
-  /* 1. element-local stages and time averages */
-  for (int e = 0; e < E; ++e) {
-    gather_elem(&m, Un, e, &W.un[e * sz]);
-    element_stages(d, &m, &W.un[e * sz], dt, &W.Rbar[e * sz], &W.Ubar[e * sz], fb, fn);
-    for (int dir = 0; dir < dim; ++dir)
-      for (size_t k = 0; k < sz; ++k) {
-        W.Fbar[((size_t)dir * E + e) * sz + k] = fb[dir * sz + k];
-        W.Fnc[((size_t)dir * E + e) * sz + k] = fn[dir * sz + k];
-      }
-  }
-  /* 2. final update, element by element, with the face terms of eq.
-   *    crkfr.non.cons.final evaluated at both faces of every direction. */
+  or_set S;
+  set_alloc(&S, E, E, sz, d->dim);
+  for (int e = 0; e < E; ++e) set_stages(d, &m, Un, dt, &S, e, e);
   for (int e = 0; e < E; ++e) {
     double unew[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
-    for (size_t k = 0; k < sz; ++k) unew[k] = W.un[e * sz + k] - dt * W.Rbar[e * sz + k];
-    for (int dir = 0; dir < dim; ++dir) {
-      for (int side = 0; side < 2; ++side) {
-        /* side 1: interface e+1/2 (element e is the '-' state); side 0: e-1/2 (e is '+') */
-        int nb = neighbour(d, e, dir, side ? +1 : -1);
-        const double *Fe = &W.Fbar[((size_t)dir * E + e) * sz], *Fn = &W.Fbar[((size_t)dir * E + nb) * sz];
-        const double *Ne = &W.Fnc[((size_t)dir * E + e) * sz], *Nn = &W.Fnc[((size_t)dir * E + nb) * sz];
-        for (int fnode = 0; fnode < np; ++fnode) {
-          int fijk[3];
-          node_ijk(&m, fnode, dim, fijk);
-          if (fijk[dir] != 0) continue;            /* enumerate face nodes once */
-          double um[OR_MAXM], up[OR_MAXM], Um[OR_MAXM], Up[OR_MAXM], Fm[OR_MAXM], Fp[OR_MAXM], Nm[OR_MAXM], Np_[OR_MAXM];
-          const double *uel = &W.un[e * sz], *unb = &W.un[nb * sz];
-          const double *Uel = &W.Ubar[e * sz], *Unb = &W.Ubar[nb * sz];
-          if (side) {   /* e is '-', nb is '+' */
-            extrapolate(d, &m, uel, dir, 1, fijk, um); extrapolate(d, &m, unb, dir, 0, fijk, up);
-            extrapolate(d, &m, Uel, dir, 1, fijk, Um); extrapolate(d, &m, Unb, dir, 0, fijk, Up);
-            extrapolate(d, &m, Fe, dir, 1, fijk, Fm);  extrapolate(d, &m, Fn, dir, 0, fijk, Fp);
-            extrapolate(d, &m, Ne, dir, 1, fijk, Nm);  extrapolate(d, &m, Nn, dir, 0, fijk, Np_);
-          } else {      /* nb is '-', e is '+' */
-            extrapolate(d, &m, unb, dir, 1, fijk, um); extrapolate(d, &m, uel, dir, 0, fijk, up);
-            extrapolate(d, &m, Unb, dir, 1, fijk, Um); extrapolate(d, &m, Uel, dir, 0, fijk, Up);
-            extrapolate(d, &m, Fn, dir, 1, fijk, Fm);  extrapolate(d, &m, Fe, dir, 0, fijk, Fp);
-            extrapolate(d, &m, Nn, dir, 1, fijk, Nm);  extrapolate(d, &m, Ne, dir, 0, fijk, Np_);
-          }
-          /* eq. numflux.cons: F^num = (F- + F+)/2 - lambda/2 (U+ - U-) */
-          double lm = wave_speed(d, dir, um), lp = wave_speed(d, dir, up);
-          double lam = lm > lp ? lm : lp;
-          double Fnum[OR_MAXM], ncs[OR_MAXM];
-          for (int v = 0; v < M; ++v) Fnum[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * lam * (Up[v] - Um[v]);
-          /* F^{num,+-}_nc = B(u^{n,+-}) g^avg(U); the jump F^num_{+-} - F^tot_{+-} */
-          double J[OR_MAXM];
-          if (side) {
-            nc_with_gavg(d, dir, um, Um, Up, ncs);
-            for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fm[v] + Nm[v]);
-          } else {
-            nc_with_gavg(d, dir, up, Um, Up, ncs);
-            for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fp[v] + Np_[v]);
-          }
-          /* - dt J d_x g_R (side 1) or - dt J d_x g_L (side 0), at every node of the line */
-          for (int p = 0; p < m.n; ++p) {
-            int ijk[3] = {fijk[0], fijk[1], fijk[2]};
-            ijk[dir] = p;
-            int id = node_id(&m, ijk, dim);
-            double dg = (side ? m.dgR[p] : m.dgL[p]) / m.dx[dir];
-            for (int v = 0; v < M; ++v) unew[id * M + v] -= dt * J[v] * dg;
-          }
-        }
-      }
-    }
+    set_update(d, &m, &S, e, dt, unew);
     for (int v = 0; v < M; ++v)
       for (int p = 0; p < np; ++p) Unew[((size_t)v * E + e) * np + p] = unew[p * M + v];
   }
-  free(W.Rbar); free(W.Ubar); free(W.Fbar); free(W.Fnc); free(W.un); free(fb); free(fn);
+  set_free(&S);
+  return 0;
+}
+
+/* Exported: the same step for nsel selected elements only (for checks of
+ * large meshes): the stages of every selected element and of its 2 dim
+ * neighbours, then the update of the selected elements.  Unew_sel receives
+ * [var][k][node] for sel[k]. */
+int or_step_elements(const or_desc *d, const double *Un, double dt, int nsel, const int *sel, double *Unew_sel) {
+  or_mesh m;
+  if (mesh_setup(d, &m)) return -1;
+  int M = m.M, np = m.np, E = m.E, dim = d->dim;
+  size_t sz = (size_t)np * M;
+  for (int k = 0; k < nsel; ++k)
+    if (sel[k] < 0 || sel[k] >= E) return -1;
+  or_set S;
+  set_alloc(&S, E, nsel * (1 + 2 * dim), sz, dim);
+  int nloc = 0;
+  for (int k = 0; k < nsel; ++k) {
+    int need[7];
+    int nn = 0;
+    need[nn++] = sel[k];
+    for (int dir = 0; dir < dim; ++dir) {
+      need[nn++] = neighbour(d, sel[k], dir, +1);
+      need[nn++] = neighbour(d, sel[k], dir, -1);
+    }
+    for (int j = 0; j < nn; ++j)
+      if (S.loc[need[j]] < 0) { set_stages(d, &m, Un, dt, &S, need[j], nloc); ++nloc; }
+  }
+  for (int k = 0; k < nsel; ++k) {
+    double unew[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
+    set_update(d, &m, &S, sel[k], dt, unew);
+    for (int v = 0; v < M; ++v)
+      for (int p = 0; p < np; ++p) Unew_sel[((size_t)v * nsel + k) * np + p] = unew[p * M + v];
+  }
+  set_free(&S);
   return 0;
 }
 

@@ -66,6 +66,7 @@ def lib():
         _lib.or_cfl_dt.argtypes = [P, D]
         _lib.or_cfl_dt.restype = ctypes.c_double
         _lib.or_step.argtypes = [P, D, ctypes.c_double, D]
+        _lib.or_step_elements.argtypes = [P, D, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), D]
         _lib.or_element_stages.argtypes = [P, D, ctypes.c_double, D, D, D, D]
         _lib.or_local_residual.argtypes = [P, D, D]
         _lib.or_fr_rhs.argtypes = [P, D, D]
@@ -177,6 +178,19 @@ def step(mesh, U, dt):
     out = np.empty_like(U)
     if lib().or_step(ctypes.byref(d), _ptr(U), float(dt), _ptr(out)):
         raise ValueError("oracle rejected the mesh descriptor")
+    return out
+
+
+def step_elements(mesh, U, dt, elems):
+    """The step's result for the listed elements only: [var][k][node] for
+    elems[k] (stages of those elements and their neighbours, then their update)."""
+    d = make_desc(mesh)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    sel = np.ascontiguousarray(elems, dtype=np.int32)
+    out = np.empty((U.shape[0], len(sel), U.shape[2]), dtype=np.float64)
+    if lib().or_step_elements(ctypes.byref(d), _ptr(U), float(dt), len(sel),
+                              sel.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(out)):
+        raise ValueError("oracle rejected the mesh descriptor or an element index")
     return out
 
 

@@ -414,19 +414,22 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
 // ---------------------------------------------------------------------------
 // Face + update kernel: one thread per node
 // ---------------------------------------------------------------------------
+// the C components of the record of face node f of face (d, side) of element e
 template <class EQ, int N, typename R>
-__device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
-                                          long long e_oth, int f, R* J, const PhysParams<R>& pp) {
-  constexpr int M = EQ::M, n = N + 1, NF = ipow(n, EQ::DIM) / n, C = trace_comps<EQ>();
-  const int side_oth = 1 - side_own;
-  R o[C], x[C];
-  const R* po = trace + trace_index<EQ, NF>(d, side_own, f, 0, E, e_own);
-  const R* px = trace + trace_index<EQ, NF>(d, side_oth, f, 0, E, e_oth);
+__device__ __forceinline__ void load_face_record(const R* __restrict__ trace, long long E, int d, int side, int f,
+                                                 long long e, R (&rec)[trace_comps<EQ>()]) {
+  constexpr int NF = ipow(N + 1, EQ::DIM) / (N + 1), C = trace_comps<EQ>();
+  const R* p = trace + trace_index<EQ, NF>(d, side, f, 0, E, e);
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    o[c] = po[(size_t)c * E];
-    x[c] = px[(size_t)c * E];
-  }
+  for (int c = 0; c < C; ++c) rec[c] = p[(size_t)c * E];
+}
+
+// Jump J = F^num - F_own [+ B(u^n_own) g^avg(U) - F^nc_own] at one face node
+// from the own record o and the other side's record x (eq. numflux.cons and
+// the reduced-communication non-conservative flux of Sec. 2.3).
+template <class EQ, typename R>
+__device__ __forceinline__ void jump_of(const R* o, const R* x, int d, int side_own, R* J, const PhysParams<R>& pp) {
+  constexpr int M = EQ::M;
   const R lam = fmax(o[2 * M], x[2 * M]);
   // own is the '-' state when it is the xi = 1 side: U+ - U- = sgn (Ux - Uo)
   const R sgn = side_own == 1 ? R(1) : R(-1);
@@ -445,6 +448,16 @@ __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long
 #pragma unroll
     for (int v = 0; v < M; ++v) J[v] -= o[2 * M + 1 + v];
   }
+}
+
+template <class EQ, int N, typename R>
+__device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
+                                          long long e_oth, int f, R* J, const PhysParams<R>& pp) {
+  constexpr int C = trace_comps<EQ>();
+  R o[C], x[C];
+  load_face_record<EQ, N, R>(trace, E, d, side_own, f, e_own, o);
+  load_face_record<EQ, N, R>(trace, E, d, 1 - side_own, f, e_oth, x);
+  jump_of<EQ, R>(o, x, d, side_own, J, pp);
 }
 
 template <class EQ, int N, typename R>

@@ -53,12 +53,21 @@ def _case(name):
         return inputs.mhd_vortex_2d(cells=(6, 5), N=N)
     if name == "mhd2d_central":
         return inputs.mhd_vortex_2d(cells=(5, 5), N=3, vol="central")
+    if name == "single2d_N3":   # one element: its own periodic neighbour in both directions
+        mesh = inputs.mesh_dict("euler", 2, 3, [1, 1], [0, 0], [1.0, 1.0], 1.4)
+        return mesh, inputs.smooth_random_field(mesh, seed=11, amp=0.2)
+    if name == "single1d_N5":
+        mesh = inputs.mesh_dict("euler", 1, 5, [1], [0], [2.0], 1.4, cfl=inputs.default_cfl(5))
+        return mesh, inputs.smooth_random_field(mesh, seed=12, amp=0.2)
+    if name == "strip2d_N2":    # one element across y
+        mesh = inputs.mesh_dict("euler", 2, 2, [37, 1], [0, 0], [2.0, 0.1], 1.4)
+        return mesh, inputs.smooth_random_field(mesh, seed=13, amp=0.2)
     raise KeyError(name)
 
 
 FP64_CASES = ["wave1d_N3", "wave1d_N1", "wave1d_N2", "wave1d_N4", "wave1d_N5", "shear2d_N3", "shear2d_N3_kep",
               "smooth2d_N1", "smooth2d_N2", "smooth2d_N4", "smooth2d_N5", "central2d_N3", "tgv3d_N3", "tgv3d_N2",
-              "mhd2d_N3", "mhd2d_N4", "mhd2d_N2", "mhd2d_central"]
+              "mhd2d_N3", "mhd2d_N4", "mhd2d_N2", "mhd2d_central", "single2d_N3", "single1d_N5", "strip2d_N2"]
 
 
 @pytest.mark.parametrize("name", FP64_CASES)

@@ -198,3 +198,25 @@ def test_linear_stability_at_cfl(orc, N):
     assert abs(rho - model) < 1e-8, (rho, model)   # central-difference error ~1e-9
     bound = {1: 1e-9, 2: 1e-9, 3: 1e-9, 4: 1e-6, 5: 5e-5}[N]
     assert rho <= 1.0 + bound, rho
+
+
+@pytest.mark.parametrize("case", ["shear2d", "mhd2d", "tgv3d"])
+def test_step_elements_equals_full_step(orc, case):
+    """The restricted step (stages of the selected elements and their
+    neighbours, then their update) runs the full step's per-element routines,
+    so on the selected elements it equals the full step bit for bit,
+    including elements on the periodic boundary."""
+    if case == "shear2d":
+        mesh, U = inputs.shear_layer_2d(cells=(7, 5), N=3)
+    elif case == "mhd2d":
+        mesh, U = inputs.mhd_vortex_2d(cells=(5, 4), N=3)
+    else:
+        mesh, U = inputs.tgv_3d(cells=(3, 4, 3), N=2, mach=0.3)
+    dt = orc.cfl_dt(mesh, U)
+    full = orc.step(mesh, U, dt)
+    E = inputs.num_elems(mesh)
+    sel = [0, E - 1, 3, E // 2, 1]
+    part = orc.step_elements(mesh, U, dt, sel)
+    assert np.array_equal(part, full[:, sel, :])
+    with pytest.raises(ValueError):
+        orc.step_elements(mesh, U, dt, [E])
