@@ -118,6 +118,19 @@ int cr_sync(cr_ctx *ctx);
  * cr_set_state).  Synchronises the stream; returns the device status. */
 int cr_get_state(cr_ctx *ctx, int solve, double *u, int u_on_device);
 
+/* Asynchronous state transfer, for host I/O that overlaps other work
+ * (pipelined serving of many problems over several contexts).  Enqueue the
+ * copy in (cr_set_state_async, which also resets t, the step counter and the
+ * status and starts the first CFL reduction, like cr_set_state) or out
+ * (cr_get_state_async) on the context's stream and return without waiting.
+ * u must stay valid and unchanged until the stream has passed the copy
+ * (cr_sync); only pinned host memory lets the copy overlap other work.  The
+ * physicality of a state copied in is reported by the next cr_sync /
+ * cr_get_state / cr_get_info, not here.  Same layout and pointer rules as
+ * cr_set_state / cr_get_state; CR_EINVAL for a bad argument. */
+int cr_set_state_async(cr_ctx *ctx, int solve, const double *u, int u_on_device);
+int cr_get_state_async(cr_ctx *ctx, int solve, double *u, int u_on_device);
+
 /* Time, last time step, steps taken and (if totals != NULL) FP64
  * quadrature-weighted domain totals: totals[0..M-1] conserved variables,
  * totals[M] kinetic energy, totals[M+1] entropy -rho s/(gamma-1),
@@ -137,7 +150,10 @@ int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes
  * CUDA events (best of 3 after a warm-up): kind 0 FP32 FMA, 1 FP64 FMA,
  * 2 MUFU reciprocal (FP32), 3 double->float conversion, 4 integer ALU
  * (lane-operations/s; an FMA counts once), 5 device copy (bytes/s read+write,
- * 2 GiB allocated for the call).  Synchronises the device. */
+ * 2 GiB allocated for the call), 6 host->device and 7 device->host copy
+ * engine with pinned host memory, 8 both directions at once (bytes/s per
+ * direction; 64 MiB pinned buffers allocated for the call).  Synchronises
+ * the device. */
 int cr_probe_peak(int kind, double *result);
 
 /* Self-check of the FP32 form's float <-> double conversions, which use

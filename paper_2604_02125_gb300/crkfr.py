@@ -39,7 +39,7 @@ _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
            "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
-           "cr_probe_peak", "cr_tuning_info", "cr_check_conversions")
+           "cr_probe_peak", "cr_tuning_info", "cr_check_conversions", "cr_set_state_async", "cr_get_state_async")
 
 
 def load_library(path=None):
@@ -58,6 +58,8 @@ def load_library(path=None):
     lib.cr_step.argtypes = [vp, ip]
     lib.cr_sync.argtypes = [vp]
     lib.cr_get_state.argtypes = [vp, ip, vp, ip]
+    lib.cr_set_state_async.argtypes = [vp, ip, vp, ip]
+    lib.cr_get_state_async.argtypes = [vp, ip, vp, ip]
     lib.cr_get_info.argtypes = [vp, ip, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp]
     lib.cr_time_kernels.argtypes = [vp, ip, vp, ctypes.c_size_t, dp]
     lib.cr_destroy.argtypes = [vp]
@@ -149,13 +151,16 @@ class Solver:
         _check(self.lib.cr_state_size(self.h, solve, ctypes.byref(nv), ctypes.byref(nn)), "cr_state_size")
         return nv.value, nn.value
 
-    def set_state(self, u, solve=0):
+    def set_state(self, u, solve=0, sync=True):
+        """Copy a state in.  sync=False: enqueue only (cr_set_state_async);
+        u must stay alive and unchanged until the next sync."""
         ptr, dev = _ptr_and_location(u)
         M, nodes = self.state_size(solve)
         count = u.size if isinstance(u, np.ndarray) else u.numel()
         if count != M * nodes:
             raise ValueError("state has %d values, expected %d" % (count, M * nodes))
-        _check(self.lib.cr_set_state(self.h, solve, ctypes.c_void_p(ptr), dev), "cr_set_state")
+        fn = self.lib.cr_set_state if sync else self.lib.cr_set_state_async
+        _check(fn(self.h, solve, ctypes.c_void_p(ptr), dev), "cr_set_state" if sync else "cr_set_state_async")
 
     def step(self, nsteps=1):
         _check(self.lib.cr_step(self.h, int(nsteps)), "cr_step")
@@ -163,13 +168,20 @@ class Solver:
     def sync(self):
         _check(self.lib.cr_sync(self.h), "cr_sync")
 
-    def get_state(self, out=None, solve=0, check=True):
+    def get_state(self, out=None, solve=0, check=True, sync=True):
+        """Copy the state out.  sync=False: enqueue only (cr_get_state_async;
+        `out` is required and holds the state after the next sync)."""
         M, nodes = self.state_size(solve)
         mesh = self.meshes[solve]
         if out is None:
+            if not sync:
+                raise ValueError("get_state(sync=False) needs an output buffer")
             from . import inputs
             out = np.empty((M, inputs.num_elems(mesh), inputs.nodes_per_elem(mesh)))
         ptr, dev = _ptr_and_location(out)
+        if not sync:
+            _check(self.lib.cr_get_state_async(self.h, solve, ctypes.c_void_p(ptr), dev), "cr_get_state_async")
+            return out
         rc = self.lib.cr_get_state(self.h, solve, ctypes.c_void_p(ptr), dev)
         if check:
             _check(rc, "cr_get_state")
@@ -244,7 +256,8 @@ def step_noalloc(mesh, u_in, u_out, dt_out=None, prec="fp64", dt_fixed=0.0, stre
     return rc
 
 
-PROBES = {"ffma": 0, "dfma": 1, "mufu_rcp": 2, "cvt_f64_f32": 3, "int_alu": 4, "copy_bytes": 5}
+PROBES = {"ffma": 0, "dfma": 1, "mufu_rcp": 2, "cvt_f64_f32": 3, "int_alu": 4, "copy_bytes": 5,
+          "h2d_bytes": 6, "d2h_bytes": 7, "duplex_bytes_per_direction": 8}
 
 
 def probe_peaks(kinds=None):

@@ -391,6 +391,29 @@ int cr_set_state(cr_ctx* c, int solve, const double* u, int u_on_device) {
   return rc;
 }
 
+int cr_set_state_async(cr_ctx* c, int solve, const double* u, int u_on_device) {
+  if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_set_state_async(c->batched, solve, u, u_on_device);
+  const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         c->stream));
+  CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
+  c->parity = 0;
+  c->lc.slot = 0;
+  CR_TRY(c->ops.lambda(c->lc, c->stream));
+  c->has_state = true;
+  return CR_OK;
+}
+
+int cr_get_state_async(cr_ctx* c, int solve, double* u, int u_on_device) {
+  if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
+  if (c->batched) return batched_get_state_async(c->batched, solve, u, u_on_device);
+  const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  CR_TRY(cudaMemcpyAsync(u, c->lc.u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         c->stream));
+  return CR_OK;
+}
+
 int cr_step(cr_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return CR_EINVAL;
   if (c->batched) return batched_step(c->batched, nsteps);

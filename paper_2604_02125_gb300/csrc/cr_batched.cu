@@ -217,13 +217,27 @@ static int status_of(const DevState& h) {
   return CR_OK;
 }
 
-int batched_set_state(BatchedCtx* b, int solve, const double* u, int on_device) {
+int batched_set_state_async(BatchedCtx* b, int solve, const double* u, int on_device) {
   LaunchCtx& lc = b->lc[solve];
   BT(cudaMemcpyAsync(lc.u, u, sizeof(double) * b->nvals[solve],
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
   BT(cudaMemsetAsync(lc.st, 0, sizeof(DevState), b->stream));
   lc.slot = b->parity;
   BT(b->ops[solve].lambda(lc, b->stream));
+  b->has_state[solve] = true;
+  return CR_OK;
+}
+
+int batched_get_state_async(BatchedCtx* b, int solve, double* u, int on_device) {
+  BT(cudaMemcpyAsync(u, b->lc[solve].u, sizeof(double) * b->nvals[solve],
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+  return CR_OK;
+}
+
+int batched_set_state(BatchedCtx* b, int solve, const double* u, int on_device) {
+  LaunchCtx& lc = b->lc[solve];
+  const int rc0 = batched_set_state_async(b, solve, u, on_device);
+  if (rc0 != CR_OK) return rc0;
   DevState h;
   BT(cudaMemcpyAsync(&h, lc.st, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
   BT(cudaStreamSynchronize(b->stream));

@@ -9,6 +9,8 @@ struct BatchedCtx;
 int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t s);
 int batched_state_size(const BatchedCtx* b, int solve, int* n_vars, long long* n_nodes);
 int batched_set_state(BatchedCtx* b, int solve, const double* u, int on_device);
+int batched_set_state_async(BatchedCtx* b, int solve, const double* u, int on_device);
+int batched_get_state_async(BatchedCtx* b, int solve, double* u, int on_device);
 int batched_step(BatchedCtx* b, int nsteps);
 int batched_sync(BatchedCtx* b);
 int batched_get_state(BatchedCtx* b, int solve, double* u, int on_device);

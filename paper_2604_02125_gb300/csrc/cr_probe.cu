@@ -146,8 +146,52 @@ extern "C" int cr_check_conversions(long long n, unsigned long long seed, long l
   return rc;
 }
 
+// host <-> device copy-engine bandwidth with pinned host memory (kinds 6-8)
+static int probe_link(int kind, double* result) {
+  const size_t bytes = (size_t)64 << 20;
+  void *h_in = nullptr, *h_out = nullptr, *d_a = nullptr, *d_b = nullptr;
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr, j2 = nullptr;
+  int rc = CR_OK;
+  if (cudaHostAlloc(&h_in, bytes, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&h_out, bytes, cudaHostAllocDefault) != cudaSuccess || cudaMalloc(&d_a, bytes) != cudaSuccess ||
+      cudaMalloc(&d_b, bytes) != cudaSuccess)
+    rc = CR_ENOMEM;
+  if (rc == CR_OK && (cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess ||
+                      cudaEventCreate(&j2) != cudaSuccess))
+    rc = CR_ECUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 5 && rc == CR_OK; ++rep) {
+    cudaEventRecord(t0, s1);
+    cudaStreamWaitEvent(s2, t0, 0);
+    if (kind == 6 || kind == 8) cudaMemcpyAsync(d_a, h_in, bytes, cudaMemcpyHostToDevice, s1);
+    if (kind == 7) cudaMemcpyAsync(h_out, d_b, bytes, cudaMemcpyDeviceToHost, s1);
+    if (kind == 8) cudaMemcpyAsync(h_out, d_b, bytes, cudaMemcpyDeviceToHost, s2);
+    cudaEventRecord(j2, s2);
+    cudaStreamWaitEvent(s1, j2, 0);
+    cudaEventRecord(t1, s1);
+    if (cudaEventSynchronize(t1) != cudaSuccess) { rc = CR_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  for (cudaEvent_t e : {t0, t1, j2})
+    if (e) cudaEventDestroy(e);
+  if (s1) cudaStreamDestroy(s1);
+  if (s2) cudaStreamDestroy(s2);
+  cudaFreeHost(h_in);
+  cudaFreeHost(h_out);
+  cudaFree(d_a);
+  cudaFree(d_b);
+  if (rc == CR_OK) *result = bytes / (best * 1e-3);
+  return rc;
+}
+
 extern "C" int cr_probe_peak(int kind, double* result) {
-  if (!result || kind < 0 || kind > 5) return CR_EINVAL;
+  if (!result || kind < 0 || kind > 8) return CR_EINVAL;
+  if (kind >= 6) return probe_link(kind, result);
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CR_ENODEV;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CR_ECUDA;

@@ -160,6 +160,11 @@ struct FaceAcc : FaceAccNc<EQ, R> {
 // limit) and the highest degree that takes the packed x/y form (above it both
 // lines' pair data no longer fit in the budget).
 constexpr int kMinB4 = 3, kMinB5 = 2, kPackMaxN = 3;
+// GLM-MHD (9 variables, 13 pair data): 2 CTAs per SM where the layout allows
+// it, which needs the shared memory of the next tile's staging buffer
+// (measured: 0.58 against 0.73 ms per volume launch at 128^2, N = 4, FP32)
+constexpr int kMinBNc = 2;
+constexpr bool kStageNc = false;
 
 template <class EQ, int N, typename R>
 struct LaneLayout {
@@ -177,8 +182,9 @@ struct LaneLayout {
   static constexpr bool PACK = PackXY<EQ>::value && sizeof(R) == 4 && N <= kPackMaxN;
   // CTAs per SM the register allocation aims at (the packed form holds both
   // lines' pair data at once)
-  static constexpr int MINB = (!EQ::NC && THREADS <= 128) ? (PACK ? 3 : 4)
-                            : (DIM == 2 && !EQ::NC) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
+  static constexpr int MINB = EQ::NC ? (2 * (bytes() + 1024) <= 228 * 1024 ? kMinBNc : 1)
+                            : (THREADS <= 128) ? (PACK ? 3 : 4)
+                            : (DIM == 2) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
 };
 
@@ -469,8 +475,9 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
 template <class EQ, int N, typename R>
 struct PersistLayout {
   using L = LaneLayout<EQ, N, R>;
+  static constexpr bool STAGE = !EQ::NC || kStageNc;
   static constexpr size_t O_STAGE = (L::bytes() + 15) & ~(size_t)15;
-  static constexpr size_t STAGE_BYTES = sizeof(double) * (size_t)EQ::M * 32 * L::NP;
+  static constexpr size_t STAGE_BYTES = STAGE ? sizeof(double) * (size_t)EQ::M * 32 * L::NP : 0;
   static constexpr size_t O_BAR = O_STAGE + STAGE_BYTES;
   static constexpr size_t bytes() { return O_BAR + 16; }
   static constexpr bool fits() { return L::fits() && bytes() <= 227 * 1024; }
@@ -491,7 +498,7 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + PL::O_BAR);
   const long long E = ma.E;
   const unsigned ntiles = (unsigned)((E + 31) / 32);
-  auto whole = [&](unsigned t) { return ma.tma_ok && (long long)(t + 1) * 32 <= E; };
+  auto whole = [&](unsigned t) { return PL::STAGE && ma.tma_ok && (long long)(t + 1) * 32 <= E; };
   auto pf_of = [&](unsigned t) {
     return Prefetch{u + (size_t)t * 32 * NP, E * NP, (unsigned)(32 * NP * sizeof(double)), staging, bar};
   };

@@ -205,3 +205,30 @@ def test_device_pointers_and_torch_stream(cr, orc):
             s.step(1)
             s.get_state(out)
     assert rel(out.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_async_transfers_pipelined(cr, prec):
+    """Three contexts on their own streams, each fed from pinned host memory
+    with the asynchronous copies (set, step, get, no host sync in between):
+    every output equals the synchronous single-context step bit for bit."""
+    import torch
+    mesh, U = inputs.shear_layer_2d(cells=(19, 13), N=3)
+    with cr.Solver(mesh, prec=prec) as s:
+        s.set_state(U)
+        s.step(2)
+        ref = s.get_state()
+    Uh = torch.from_numpy(U).pin_memory()
+    outs = [torch.empty_like(Uh).pin_memory() for _ in range(3)]
+    solvers = [cr.Solver(mesh, prec=prec, stream=torch.cuda.Stream()) for _ in range(3)]
+    for it in range(6):
+        s = solvers[it % 3]
+        s.set_state(Uh, sync=False)
+        s.step(2)
+        s.get_state(outs[it % 3], sync=False)
+    for s in solvers:
+        s.sync()
+        s.close()
+    for o in outs:
+        assert np.array_equal(o.numpy(), ref)
+
