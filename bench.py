@@ -193,8 +193,24 @@ def run_batched(crkfr, inputs, stream, steps):
     info = b.tuning_info()
     status = b.info(solve=0)["status"]
     b.close()
+    # roofline of the per-degree volume kernels: counted FP32 flops of every
+    # solve of that degree / the kernel's autotuned launch time
+    stages = {1: 2, 2: 3, 3: 4, 4: 6, 5: 7}
+    flops = {}
+    for m in meshes:
+        flops[m["N"]] = flops.get(m["N"], 0) + volume_flops_2d(inputs.num_elems(m), m["N"], stages[m["N"]])
+    peaks = _peaks()
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    vol_roof = {}
+    for N, f in sorted(flops.items()):
+        t = info.get("N%d_volume" % N, {}).get("ms")
+        if t:
+            vol_roof["N%d" % N] = {"tflops": f / (t * 1e-3) / 1e12, "frac": f / (t * 1e-3) / 1e12 / fp32_peak,
+                                   "gflop_per_launch": f / 1e9, "ms_per_launch": t}
     return {"value": nodes / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "solves": len(meshes),
             "nodes": nodes, "status": crkfr.status_string(status), "tuning": info,
+            "volume_roofline": dict(vol_roof, bound="alu", peak_tflops=fp32_peak,
+                                    note="launch times from the autotuner (best of two, warm L2)"),
             "workload": "512 independent 2D Euler solves, sides 16..128 quads, N in {2,3,4,5}, seeded smooth "
                         "densities (amplitude 0.1-0.5) and shear, FP32 pair fluxes, FP64 update"}
 
@@ -206,6 +222,7 @@ ORACLE_SAMPLES = {
     "wave1d_64_N3": ("density_wave_1d", dict(cells=64, N=3), 2000),
     "shear2d_256_N3": ("shear_layer_2d", dict(cells=(32, 32), N=3), 40),
     "shear2d_256_N3_kep": ("shear_layer_2d", dict(cells=(32, 32), N=3, vol="kep"), 40),
+    "shear2d_256_N3_central": ("shear_layer_2d", dict(cells=(32, 32), N=3, vol="central"), 40),
     "mhd2d_128_N4": ("mhd_vortex_2d", dict(cells=(16, 16), N=4), 40),
     "tgv3d_64_N3": ("tgv_3d", dict(cells=(8, 8, 8), N=3), 20),
 }

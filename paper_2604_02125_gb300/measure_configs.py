@@ -31,6 +31,8 @@ WORKLOADS = {
                        "2D Euler shear layer, 256x256 quads, N=3, EC flux"),
     "shear2d_256_N3_kep": (lambda: inputs.shear_layer_2d(cells=(256, 256), N=3, vol="kep"),
                            "2D Euler shear layer, 256x256 quads, N=3, KEP flux"),
+    "shear2d_256_N3_central": (lambda: inputs.shear_layer_2d(cells=(256, 256), N=3, vol="central"),
+                               "2D Euler shear layer, 256x256 quads, N=3, central two-point flux (collocation FR)"),
     "mhd2d_128_N4": (lambda: inputs.mhd_vortex_2d(cells=(128, 128), N=4),
                      "2D GLM-MHD vortex, 128x128 quads, N=4, EC flux"),
     "tgv3d_64_N3": (lambda: inputs.tgv_3d(cells=(64, 64, 64), N=3), "3D Euler Taylor-Green vortex, 64^3 hexes, N=3"),
