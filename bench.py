@@ -137,6 +137,7 @@ def job_value(nodes_per_rank, steps, world, job_ms):
 
 
 VOLUME_PROFILE = os.path.join(ROOT, "profiles", "k_volume_lanes_shear2d_256x256_N3_fp32.md")
+FACE_PROFILE = os.path.join(ROOT, "profiles", "k_face_update_lanes_shear2d_256x256_N3_fp32.md")
 
 
 def time_steps(solver, steps, stream, flush):
@@ -420,6 +421,21 @@ def main():
                     "traffic_source": os.path.relpath(VOLUME_PROFILE, ROOT) if prof else "no capture of these sources",
                     "kernel": "k_volume_lanes<Euler<2>,3,float>", "flops_per_launch": vflops,
                     "ms_per_launch": vol_ms, "face_update_ms_per_launch": face_ms}
+        if face_ms:
+            # face/update kernel against HBM: algorithmic bytes per DOF-update
+            # (2D Euler, FP32 form) = u read 32 + Rbar read 16 + own face
+            # records 2 dirs x 2 sides x (N+1) face nodes x C comps x 4 B / (N+1)^2
+            # nodes + u written 32 (the neighbours' records are the same data)
+            C = 2 * 4 + 1
+            rec = 2 * 2 * (N_DEG + 1) * C * 4 / (N_DEG + 1) ** 2
+            fbytes = nodes * (32 + 16 + rec + 32)
+            hbm = peaks.get("hbm_gbs")
+            fprof = profile_summary.read_profile_traffic(FACE_PROFILE)
+            roofline["face_update"] = {
+                "bound": "hbm", "achieved": fbytes / (face_ms * 1e-3) / 1e9, "unit": "GB/s",
+                "peak": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm else None,
+                "frac": (fbytes / (face_ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                "bytes_per_launch": fbytes, "traffic": fprof[1] if fprof else None}
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -162,8 +162,10 @@ int cr_probe_peak(int kind, double *result);
  * counterpart.  Converts n seeded bit patterns (half of the doubles with
  * exponents confined to the FP32 range and its edges, plus infinities and
  * NaNs) both ways on the current device and stores in *mismatches how many
- * results differ from the hardware conversion; inputs below the normal FP32
- * range are expected to give signed zero.  Returns CR_EINVAL for n < 0 or a
+ * results differ from the hardware conversion (round to nearest both ways,
+ * and the round-toward-zero conversion of the FP32 physicality check, which
+ * gives NaN from 2^128 on); inputs below the normal FP32 range are expected
+ * to give signed zero.  Returns CR_EINVAL for n < 0 or a
  * NULL pointer, CR_ENOMEM/CR_ECUDA on a device error.  Synchronises. */
 int cr_check_conversions(long long n, unsigned long long seed, long long *mismatches);
 

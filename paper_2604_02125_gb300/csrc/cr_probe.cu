@@ -113,6 +113,13 @@ __global__ void __launch_bounds__(256) k_check_cvt(long long n, unsigned long lo
     if (x != x) ok = mine != mine;
     else if (below) ok = __float_as_uint(mine) == (unsigned)((db >> 32) & 0x80000000ull);
     else ok = __float_as_uint(mine) == __float_as_uint(hw);
+    // round-toward-zero conversion of the physicality check: the hardware's
+    // __double2float_rz in the normal FP32 range, signed zero below, NaN above
+    const float rz = crk::d2f_rz(x);
+    bool okz;
+    if (((db >> 52) & 0x7FFull) >= 1151ull) okz = rz != rz;   // |x| >= 2^128, infinities, NaNs
+    else if (below) okz = __float_as_uint(rz) == (unsigned)((db >> 32) & 0x80000000ull);
+    else okz = __float_as_uint(rz) == __float_as_uint(__double2float_rz(x));
     const unsigned fb = (unsigned)(r >> 17);
     const float f = __uint_as_float(fb);
     const double hwd = (double)f, mined = crk::f2d_int(f);
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(256) k_check_cvt(long long n, unsigned long lo
     if (f != f) okd = mined != mined;
     else if (((fb >> 23) & 0xFFu) == 0u) okd = __double_as_longlong(mined) == (long long)((unsigned long long)(fb & 0x80000000u) << 32);
     else okd = __double_as_longlong(mined) == __double_as_longlong(hwd);
-    cnt += (ok ? 0u : 1u) + (okd ? 0u : 1u);
+    cnt += (ok ? 0u : 1u) + (okd ? 0u : 1u) + (okz ? 0u : 1u);
   }
   if (cnt) atomicAdd(bad, cnt);
 }

@@ -405,7 +405,7 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
   } else {
     float uf[EQ::M];
 #pragma unroll
-    for (int v = 0; v < EQ::M; ++v) uf[v] = d2f_int(uu[v]);
+    for (int v = 0; v < EQ::M; ++v) uf[v] = d2f_rz(uu[v]);
     if constexpr (EQ::NC) return EQ::physical(uf, ma.gamma_f, ma.c_h_f, lam, ma.inv_dx_f);
     else return EQ::physical(uf, ma.gamma_f, lam, ma.inv_dx_f);
   }

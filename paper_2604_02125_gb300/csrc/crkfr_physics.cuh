@@ -150,6 +150,21 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Double -> float rounded toward zero, for the FP32 physicality and wave-speed
+// check of an updated state (a sign test and a maximum: the rounding
+// direction does not matter there).  Values below the normal FP32 range give
+// signed zero; values beyond it, infinities and NaNs give NaN, which fails the
+// check.  About ten integer instructions against twenty-five for d2f_int.
+__device__ __forceinline__ float d2f_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mant = __funnelshift_r(lo, hi, 29) & 0x7FFFFFu;
+  const unsigned sign = hi & 0x80000000u;
+  unsigned bits = sign | ((e - 896u) << 23) | mant;
+  bits = e - 897u < 254u ? bits : (e < 897u ? sign : 0x7FC00000u);
+  return __uint_as_float(bits);
+}
+
 // Reciprocal and square root of the CFL wave speeds: IEEE in FP64, the MUFU
 // approximations (about 1 ulp) in FP32, where the result only enters the
 // maximum that sets dt.
