@@ -121,6 +121,26 @@ __device__ __forceinline__ void logmean_pair(float a1, float b1, float a2, float
   }
 }
 
+// FP64: the same single-reciprocal form (each FP64 division is a dozen
+// instructions on the narrow FP64 pipe): 1/F(u) by its own series, five terms
+// (truncation below 1e-21 for u < 1e-4), and 1/s1, 1/s2 from 1/(s1 s2).
+__device__ __forceinline__ double series_invF(double u) {
+  return 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0 + u * (-428.0 / 14175.0))));
+}
+__device__ __forceinline__ void logmean_pair(double a1, double b1, double a2, double b2, double& L1, double& iL2) {
+  const double s1 = a1 + b1, d1 = a1 - b1, s2 = a2 + b2, d2 = a2 - b2;
+  const double r = 1.0 / (s1 * s2);
+  const double rs1 = s2 * r, rs2 = s1 * r;
+  const double f1 = d1 * rs1, f2 = d2 * rs2;
+  const double u1 = f1 * f1, u2 = f2 * f2;
+  if (fmax(u1, u2) < LogMeanEps<double>::v) {
+    L1 = 0.5 * s1 * series_invF(u1);
+    iL2 = 2.0 * series_F(u2) * rs2;
+  } else {
+    logmean_pair_general(a1, b1, a2, b2, L1, iL2);
+  }
+}
+
 // Exact float <-> double conversions with integer instructions only (the FP64
 // pipe of this GPU is narrow and also executes the hardware conversions, and a
 // predicated hardware fallback would still occupy it).  Values below the
@@ -194,6 +214,23 @@ struct Euler {
   template <typename R>
   __device__ __forceinline__ static void pair_data(const R* u, R* q, const PhysParams<R>& pp) {
     R rho = u[0];
+    R E = u[DIM + 1];
+    if constexpr (sizeof(R) == 8 && VOL == VOL_EC) {
+      // one FP64 division for 1/rho and rho/p: p needs |m|^2 / rho, so
+      // p rho = (gamma-1)(E rho - |m|^2/2) and 1/(rho p rho) gives both
+      R mm = R(0);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) mm += u[1 + k] * u[1 + k];
+      const R prho = (pp.gamma - R(1)) * (E * rho - R(0.5) * mm);   // p rho
+      const R r = R(1) / (prho * rho);
+      const R ir = prho * r;                                         // 1 / rho
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) q[1 + k] = u[1 + k] * ir;
+      q[0] = rho;
+      q[IP] = prho * ir;
+      q[IAUX] = rho * rho * rho * r;                                 // rho / p
+      return;
+    }
     R ir = fast_rcp(rho);
     R ke = R(0);
     q[0] = rho;
@@ -203,7 +240,6 @@ struct Euler {
       q[1 + k] = v;
       ke += v * u[1 + k];
     }
-    R E = u[DIM + 1];
     R p = (pp.gamma - R(1)) * (E - R(0.5) * ke);
     q[IP] = p;
     if constexpr (VOL == VOL_EC) q[IAUX] = rho * fast_rcp(p);
@@ -328,15 +364,29 @@ struct GlmMhd {
   template <typename R>
   __device__ __forceinline__ static void pair_data(const R* u, R* q, const PhysParams<R>& pp) {
     R rho = u[0];
-    R ir = fast_rcp(rho);
-    R v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
     R B1 = u[5], B2 = u[6], B3 = u[7], psi = u[8];
-    R vv = v1 * v1 + v2 * v2 + v3 * v3;
     R BB = B1 * B1 + B2 * B2 + B3 * B3;
-    R p = (pp.gamma - R(1)) * (u[4] - R(0.5) * rho * vv - R(0.5) * BB - R(0.5) * psi * psi);
+    R ir, p, irp;   // 1/rho, p, rho/p
+    if constexpr (sizeof(R) == 8) {
+      // one FP64 division: p rho = (gamma-1)(rho (E - |B|^2/2 - psi^2/2) - |m|^2/2)
+      const R mm = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+      const R prho = (pp.gamma - R(1)) * (rho * (u[4] - R(0.5) * BB - R(0.5) * psi * psi) - R(0.5) * mm);
+      const R r = R(1) / (prho * rho);
+      ir = prho * r;
+      p = prho * ir;
+      irp = rho * rho * rho * r;
+    } else {
+      ir = fast_rcp(rho);
+      const R w1 = u[1] * ir, w2 = u[2] * ir, w3 = u[3] * ir;
+      const R vv0 = w1 * w1 + w2 * w2 + w3 * w3;
+      p = (pp.gamma - R(1)) * (u[4] - R(0.5) * rho * vv0 - R(0.5) * BB - R(0.5) * psi * psi);
+      irp = rho * fast_rcp(p);
+    }
+    R v1 = u[1] * ir, v2 = u[2] * ir, v3 = u[3] * ir;
+    R vv = v1 * v1 + v2 * v2 + v3 * v3;
     q[0] = rho; q[1] = v1; q[2] = v2; q[3] = v3; q[4] = p;
     q[5] = B1; q[6] = B2; q[7] = B3; q[8] = psi;
-    q[IBETA] = R(0.5) * rho * fast_rcp(p);
+    q[IBETA] = R(0.5) * irp;
     q[IV2] = vv; q[IB2] = BB; q[IVB] = v1 * B1 + v2 * B2 + v3 * B3;
   }
 
