@@ -160,6 +160,9 @@ struct FaceAcc : FaceAccNc<EQ, R> {
 // limit) and the highest degree that takes the packed x/y form (above it both
 // lines' pair data no longer fit in the budget).
 constexpr int kMinB4 = 3, kMinB5 = 2, kPackMaxN = 3;
+// degree 2, FP32: short lines, little per-thread state; 8 CTAs per SM (measured
+// 0.50 -> 0.42 ms per batched volume launch against 3)
+constexpr int kMinB2 = 8;
 // GLM-MHD (9 variables, 13 pair data): 2 CTAs per SM where the layout allows
 // it, which needs the shared memory of the next tile's staging buffer
 // (measured: 0.58 against 0.73 ms per volume launch at 128^2, N = 4, FP32)
@@ -183,7 +186,7 @@ struct LaneLayout {
   // CTAs per SM the register allocation aims at (the packed form holds both
   // lines' pair data at once)
   static constexpr int MINB = EQ::NC ? (2 * (bytes() + 1024) <= 228 * 1024 ? kMinBNc : 1)
-                            : (THREADS <= 128) ? (PACK ? 3 : 4)
+                            : (THREADS <= 128) ? ((N == 2 && sizeof(R) == 4) ? kMinB2 : PACK ? 3 : 4)
                             : (DIM == 2) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
 };
