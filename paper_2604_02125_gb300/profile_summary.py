@@ -84,6 +84,9 @@ KERNEL_METRICS = [
     ("DRAM read", "dram__bytes_read.sum"),
     ("DRAM write", "dram__bytes_write.sum"),
     ("DRAM throughput % of peak", "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+    ("L2 sector hit rate (bytes served by L2 are not HBM traffic)", "lts__t_sector_hit_rate.pct"),
+    ("L2 read hit rate", "lts__t_sector_op_read_hit_rate.pct"),
+    ("L1 sector hit rate", "l1tex__t_sector_hit_rate.pct"),
     ("registers / thread", "launch__registers_per_thread"),
     ("block size", "launch__block_size"),
     ("grid size", "launch__grid_size"),
