@@ -142,8 +142,9 @@ int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps,
  * before every step, if flush_buf != NULL, flush_bytes of that device buffer
  * are overwritten (cudaMemsetAsync) to evict the L2.  ms[0] receives the mean
  * duration of one volume-kernel launch, ms[1] of one face/update launch (the
- * batched form: ms[0] = one persistent step launch, ms[1] = 0).  The state
- * advances exactly as with cr_step.  Synchronises the stream. */
+ * batched form: ms[0] = the volume launches of all degrees of one step, ms[1]
+ * = their face/update launches).  The state advances exactly as with
+ * cr_step.  Synchronises the stream. */
 int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
 
 /* Measurement: throughput of one unit on the current device, measured with
