@@ -188,6 +188,7 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
     }
     // untuned default: one CTA per tile
     g.vol.grid = g.face.grid = (int)g.ntiles;
+    g.vol.shape = g.face.shape = 0;
     b->groups.push_back(g);
     if (rc != CR_OK) break;
   }
@@ -303,31 +304,39 @@ static int autotune(BatchedCtx* b) {
     for (int which = 0; which < 2; ++which) {
       BatchLaunch& bl = which == 0 ? g.vol : g.face;
       auto fn = which == 0 ? g.ops.vol_batched : g.ops.face_batched;
-      const int occ = std::max(1, g.ops.occupancy(which));
-      std::vector<int> cands;
-      for (int c = 1; c <= occ; ++c) cands.push_back(std::min((int)g.ntiles, c * b->sms));
-      cands.push_back((int)g.ntiles);
-      std::sort(cands.begin(), cands.end());
-      cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-      int best = cands.back();
+      // candidates: every kernel shape (volume) x every persistent grid of
+      // 1 .. resident CTAs per SM times the SM count, and one CTA per tile
+      const int shapes = which == 0 ? std::max(1, g.ops.vol_shapes) : 1;
+      int best = (int)g.ntiles, best_shape = 0;
       float best_ms = 1e30f;
-      for (int grid : cands) {
-        bl.grid = grid;
-        float ms = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {   // first run warms up
-          float t = time_launch(b, fn, bl, t0, t1);
-          if (rep > 0) ms = std::min(ms, t);
-          if (which == 1) {   // undo the update of the face trial
-            cudaMemcpyAsync(b->u, u_save, sizeof(double) * b->total_u, cudaMemcpyDeviceToDevice, b->stream);
-            cudaMemcpyAsync(b->st, st_save, sizeof(DevState) * b->n, cudaMemcpyDeviceToDevice, b->stream);
+      for (int shape = 0; shape < shapes; ++shape) {
+        bl.shape = shape;
+        const int occ = std::max(1, g.ops.occupancy(which, shape));
+        std::vector<int> cands;
+        for (int c = 1; c <= occ; ++c) cands.push_back(std::min((int)g.ntiles, c * b->sms));
+        cands.push_back((int)g.ntiles);
+        std::sort(cands.begin(), cands.end());
+        cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+        for (int grid : cands) {
+          bl.grid = grid;
+          float ms = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {   // first run warms up
+            float t = time_launch(b, fn, bl, t0, t1);
+            if (rep > 0) ms = std::min(ms, t);
+            if (which == 1) {   // undo the update of the face trial
+              cudaMemcpyAsync(b->u, u_save, sizeof(double) * b->total_u, cudaMemcpyDeviceToDevice, b->stream);
+              cudaMemcpyAsync(b->st, st_save, sizeof(DevState) * b->n, cudaMemcpyDeviceToDevice, b->stream);
+            }
           }
+          if (ms < best_ms) { best_ms = ms; best = grid; best_shape = shape; }
         }
-        if (ms < best_ms) { best_ms = ms; best = grid; }
       }
       bl.grid = best;
-      std::snprintf(buf, sizeof(buf), "%s\"N%d_%s\": {\"grid\": %d, \"ctas_per_sm\": %.2f, \"ms\": %.4f, \"tiles\": %u}",
+      bl.shape = best_shape;
+      std::snprintf(buf, sizeof(buf),
+                    "%s\"N%d_%s\": {\"grid\": %d, \"ctas_per_sm\": %.2f, \"shape\": %d, \"ms\": %.4f, \"tiles\": %u}",
                     b->tuning.size() > 1 ? ", " : "", g.N, which == 0 ? "volume" : "face", best,
-                    (double)best / b->sms, best_ms, g.ntiles);
+                    (double)best / b->sms, best_shape, best_ms, g.ntiles);
       b->tuning += buf;
     }
   }

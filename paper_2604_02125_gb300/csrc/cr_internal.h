@@ -35,6 +35,7 @@ struct BatchLaunch {
   RefTab<double> tb64;
   RefTab<float> tb32;
   int slot;           // step parity (as LaunchCtx::slot)
+  int shape;          // volume kernel shape (0: default, 1: alternative; chosen by the autotuner)
 };
 
 struct VariantOps {
@@ -51,7 +52,8 @@ struct VariantOps {
   // batched persistent kernels (2D Euler only; null elsewhere)
   cudaError_t (*vol_batched)(const BatchLaunch&, cudaStream_t);
   cudaError_t (*face_batched)(const BatchLaunch&, cudaStream_t);
-  int (*occupancy)(int which);   // resident CTAs per SM: 0 = volume, 1 = face
+  int (*occupancy)(int which, int shape);   // resident CTAs per SM: 0 = volume, 1 = face
+  int vol_shapes;               // volume kernel shapes of the batched form
   int threads_vol, threads_face;
 };
 

@@ -103,8 +103,11 @@ struct Variant {
     }
     if constexpr (kLanes) {
       if constexpr (kBatched) {
-        cudaError_t e = cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)PL::bytes());
+        cudaError_t e = cudaFuncSetAttribute(k_volume_batched<EQ, N, R, 0>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_volume_batched<EQ, N, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PL::bytes());
         if (e != cudaSuccess) return e;
       }
       return cudaFuncSetAttribute(k_volume_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -114,8 +117,12 @@ struct Variant {
   }
   static cudaError_t vol_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
-      k_volume_batched<EQ, N, R><<<b.grid, LL::THREADS, PL::bytes(), s>>>(
-          b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b), b.slot);
+      if (b.shape == 1)
+        k_volume_batched<EQ, N, R, 1><<<b.grid, LL::THREADS, PL::bytes(), s>>>(
+            b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b), b.slot);
+      else
+        k_volume_batched<EQ, N, R, 0><<<b.grid, LL::THREADS, PL::bytes(), s>>>(
+            b.solves, b.tiles, b.ntiles, PPB<R>::get(b), PPB<R>::tab(b), b.slot);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -128,12 +135,13 @@ struct Variant {
     }
     return cudaErrorNotSupported;
   }
-  static int occupancy(int which) {
+  static int occupancy(int which, int shape) {
     int nb = 0;
     if constexpr (kBatched) {
       if (which == 0) {
-        cudaFuncSetAttribute(k_volume_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_batched<EQ, N, R>, LL::THREADS, PL::bytes());
+        auto k = shape == 1 ? k_volume_batched<EQ, N, R, 1> : k_volume_batched<EQ, N, R, 0>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, LL::THREADS, PL::bytes());
       } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_face_batched<EQ, N, R>, FL::THREADS, FL::bytes());
       }
@@ -144,6 +152,7 @@ struct Variant {
     o->vol_batched = kBatched ? &vol_batched : nullptr;
     o->face_batched = kBatched ? &face_batched : nullptr;
     o->occupancy = kBatched ? &occupancy : nullptr;
+    o->vol_shapes = kBatched ? 2 : 0;
     o->threads_vol = LL::THREADS;
     o->threads_face = FL::THREADS;
     o->M = EQ::M;

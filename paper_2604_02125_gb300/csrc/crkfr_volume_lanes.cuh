@@ -169,8 +169,15 @@ constexpr int kMinB2 = 8;
 constexpr int kMinBNc = 2;
 constexpr bool kStageNc = false;
 
+// Kernel shapes: SH = 0 is the measured default of each variant; SH = 1 is the
+// alternative the batched form's autotuner also times: the scalar form (no
+// x/y packing) at one resident CTA per SM more than the packed default, or,
+// for a scalar default, one fewer (fewer spills, fewer warps).
+template <class EQ, int N, typename R, int SH = 0>
+struct LaneLayout;
+
 template <class EQ, int N, typename R>
-struct LaneLayout {
+struct LaneLayout<EQ, N, R, 0> {
   static constexpr int DIM = EQ::DIM, M = EQ::M, P = EQ::P, n = N + 1;
   static constexpr int NP = ipow(n, DIM), NF = NP / n, S = rk_stages(N);
   static constexpr int O_Q = 0;                                // [P][NP] pair data (also staging)
@@ -189,6 +196,13 @@ struct LaneLayout {
                             : (THREADS <= 128) ? ((N == 2 && sizeof(R) == 4) ? kMinB2 : PACK ? 3 : 4)
                             : (DIM == 2) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
+};
+
+template <class EQ, int N, typename R>
+struct LaneLayout<EQ, N, R, 1> : LaneLayout<EQ, N, R, 0> {
+  using B = LaneLayout<EQ, N, R, 0>;
+  static constexpr bool PACK = false;
+  static constexpr int MINB = B::PACK ? B::MINB + 1 : (B::MINB > 1 ? B::MINB - 1 : 1);
 };
 
 template <class EQ, int N, typename R, int D>
@@ -280,13 +294,13 @@ __device__ __forceinline__ void issue_prefetch(const Prefetch& pf) {
 // One tile of 32 elements starting at e0 (the CTA's whole shared memory sm).
 // staged != nullptr: u^n of the tile already sits in shared memory as FP64,
 // [var][32][NP] (the tile's slice of the global layout).
-template <class EQ, int N, typename R>
+template <class EQ, int N, typename R, int SH = 0>
 __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
                                                   R* __restrict__ trace, const DevState* __restrict__ st,
                                                   const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
                                                   long long e0, R dtR, R* sm, const double* staged = nullptr,
                                                   Prefetch pf = Prefetch{nullptr, 0, 0, nullptr, nullptr}) {
-  using L = LaneLayout<EQ, N, R>;
+  using L = LaneLayout<EQ, N, R, SH>;
   constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
   constexpr int NS = rk_nsaved(N) > 0 ? rk_nsaved(N) : 1;
 
@@ -724,8 +738,8 @@ struct BatchTile {
   unsigned e0;
 };
 
-template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+template <class EQ, int N, typename R, int SH = 0>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R, SH>::THREADS, LaneLayout<EQ, N, R, SH>::MINB)
 k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restrict__ tiles, unsigned ntiles,
                  const PhysParams<R> pp, const RefTab<R> tb, int slot) {
   using PL = PersistLayout<EQ, N, R>;
@@ -772,7 +786,7 @@ k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restr
     __shared__ double s_dt;
     if (threadIdx.x == 0) s_dt = step_begin(bs.st, slot, ma.cfl, ma.dt_fixed, t.e0 == 0);
     __syncthreads();
-    volume_lanes_tile<EQ, N, R>(bs.u, (R*)bs.rbar, (R*)bs.trace, bs.st, ma, pp, tb, (long long)t.e0,
+    volume_lanes_tile<EQ, N, R, SH>(bs.u, (R*)bs.rbar, (R*)bs.trace, bs.st, ma, pp, tb, (long long)t.e0,
                                 dt_as<R>(s_dt), sm, staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }

@@ -52,8 +52,12 @@ def test_batch_matches_single_solves(cr, prec):
             s.step(5)
             ref = s.get_state()
             info = s.info()
-        assert rel(outs[k], ref) <= 1e-14, (k, m["N"], rel(outs[k], ref))
-        assert infos[k]["steps"] == 5 and abs(infos[k]["t"] - info["t"]) <= 1e-15 * info["t"]
+        # the same kernels give the same result to round-off; where the
+        # autotuner picked the alternative shape (the scalar instead of the
+        # packed FP32 form), the two are different FP32 evaluations
+        alt = tun["N%d_volume" % m["N"]]["shape"] != 0 and prec == "fp32"
+        assert rel(outs[k], ref) <= (1e-6 if alt else 1e-14), (k, m["N"], rel(outs[k], ref))
+        assert infos[k]["steps"] == 5 and abs(infos[k]["t"] - info["t"]) <= (1e-6 if alt else 1e-15) * info["t"]
 
 
 def test_batch_fp64_vs_oracle_per_solve_dt(cr, orc):
