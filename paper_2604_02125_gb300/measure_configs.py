@@ -8,7 +8,8 @@ fluxes) prints one JSON line: DOF-updates/s over K steps timed with CUDA
 events on the solver's stream (256 MiB L2 flush between steps), the mean
 volume and face/update kernel times, the FP32-vs-FP64 relative L2 after 100
 steps from the same state, and for the Taylor-Green vortex the FP64 kinetic
-energy and entropy budgets over S steps.
+energy and entropy budgets over S steps; and the shear layer over its full
+run length (--long-steps, 2000): FP32 against FP64, conservation, budgets.
 
 The headline measurement is bench.py (whose --cpu-baseline-configs option
 times the FP64 oracle on reduced meshes of the same workloads); this script
@@ -100,6 +101,35 @@ def measure_gpu(name, make, desc, steps, budget_steps):
     return out
 
 
+def measure_long(steps):
+    """The shear layer over its full run length: FP32 pair-flux form against the
+    FP64 path (itself pinned to the oracle per step), FP64 totals of both."""
+    import torch
+    mesh, U = inputs.shear_layer_2d(cells=(256, 256), N=3)
+    out = {"workload": "shear2d_256_N3_long", "steps": steps, "forms": {}}
+    finals = {}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for prec in ("fp64", "fp32"):
+            s = crkfr.Solver(mesh, prec=prec, stream=stream)
+            s.set_state(U)
+            i0 = s.info(totals=True)
+            s.step(steps)
+            i1 = s.info(totals=True)
+            finals[prec] = s.get_state(check=False)
+            M = int(U.shape[0])
+            scale = np.abs(U).reshape(M, -1).sum(axis=1) / U[0].size
+            out["forms"][prec] = {
+                "status": crkfr.status_string(i1["status"]), "t": i1["t"],
+                "conservation_rel": [float(abs(i1["totals"][v] - i0["totals"][v]) / max(abs(i0["totals"][v]), scale[v]))
+                                     for v in range(M)],
+                "kinetic_energy_rel_change": float((i1["totals"][M] - i0["totals"][M]) / abs(i0["totals"][M])),
+                "entropy_rel_change": float((i1["totals"][M + 1] - i0["totals"][M + 1]) / abs(i0["totals"][M + 1]))}
+            s.close()
+    out["rel_l2_fp32_vs_fp64"] = float(np.linalg.norm(finals["fp32"] - finals["fp64"]) / np.linalg.norm(finals["fp64"]))
+    return out
+
+
 def measure_batched(steps):
     import torch
     specs = inputs.batched_2d_specs()
@@ -132,11 +162,15 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--budget-steps", type=int, default=500)
     ap.add_argument("--only", nargs="*", default=None)
+    ap.add_argument("--long-steps", type=int, default=2000, help="run length of the shear-layer long run (0: skip)")
     a = ap.parse_args(argv)
-    names = a.only or list(WORKLOADS) + ["batched2d_512"]
+    names = a.only or list(WORKLOADS) + ["batched2d_512", "shear2d_256_N3_long"]
     build.build()
     for name in names:
-        if name == "batched2d_512":
+        if name == "shear2d_256_N3_long":
+            if a.long_steps > 0:
+                print(json.dumps(measure_long(a.long_steps)), flush=True)
+        elif name == "batched2d_512":
             print(json.dumps(measure_batched(max(3, min(a.steps, 10)))), flush=True)
         else:
             make, desc = WORKLOADS[name]
