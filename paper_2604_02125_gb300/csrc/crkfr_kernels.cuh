@@ -1,6 +1,8 @@
-// crkfr_kernels.cuh -- the three kernels of one cRKFR step on sm_103a.
+// crkfr_kernels.cuh -- shared pieces of the cRKFR step kernels on sm_103a,
+// and the general (tile-form) kernels that serve the variants whose lane form
+// (crkfr_volume_lanes.cuh) does not fit in shared memory.
 //
-//  k_volume       element-local cRK stages (eq. crkfr.inner) with the
+//  k_volume_tile  element-local cRK stages (eq. crkfr.inner) with the
 //                 flux-differencing local residual (Sec. 3, eqs.
 //                 entropy.cons.flux.dev, entropy.cons.noncons.dev), the
 //                 b-weighted volume residual of the final update (Sec. 3,
@@ -8,15 +10,19 @@
 //                 time averages U, F (eq. disc.avg.flux), F^nc (Sec. 2.3) and
 //                 of lambda(u^n).  One CTA holds `epb` elements in shared
 //                 memory; one thread per line (N+1 nodes along a direction).
-//  k_face_update  the single inter-element step: per face node one
-//                 time-averaged Rusanov flux (eq. numflux.cons) and the
-//                 reduced-communication non-conservative flux B(u^{n,+-})
-//                 g^avg(U) (Sec. 2.3), applied through the g2 correction
-//                 derivatives g_R'(1) = 1/w_N, g_L'(0) = -1/w_0 (GLL + g2) in
-//                 the FP64 update (eq. crkfr.non.cons.final); then the CFL
-//                 reduction for the next dt and the physicality flag.
+//  k_face_update  the single inter-element step, one thread per node: per face
+//                 node one time-averaged Rusanov flux (eq. numflux.cons) and
+//                 the reduced-communication non-conservative flux
+//                 B(u^{n,+-}) g^avg(U) (Sec. 2.3), applied through the g2
+//                 correction derivatives g_R'(1) = 1/w_N, g_L'(0) = -1/w_0
+//                 (GLL + g2) in the FP64 update (eq. crkfr.non.cons.final);
+//                 then the CFL reduction of the new state and the
+//                 physicality flag.
 //  k_lambda       CFL reduction of a state (first step after set_state).
 //  k_totals       FP64 quadrature-weighted totals (diagnostics).
+// Shared: the mesh and reference-element parameters, the step record and its
+// fence-free CFL protocol (reduce_lambda / step_begin), element coordinates
+// and periodic neighbours, the face-record layout and the Rusanov jump.
 //
 // Layouts in HBM:
 //   u     [M][E][NP] FP64        state, updated in place by k_face_update

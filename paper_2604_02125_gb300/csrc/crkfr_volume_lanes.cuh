@@ -1,4 +1,6 @@
-// crkfr_volume_lanes.cuh -- volume kernel, lane form (sm_103a).
+// crkfr_volume_lanes.cuh -- the lane-form kernels of the cRKFR step (sm_103a):
+// the persistent volume kernel (single solve and batched), the face/update
+// kernel (single solve and batched) and their shared-memory layouts.
 //
 // Same computation as k_volume_tile (element-local cRK stages with the
 // flux-differencing residual, the b-weighted volume residual and the face
@@ -18,7 +20,12 @@
 //  * 2D Euler in FP32 (N <= 3): the thread's x-line and y-line are
 //    flux-differenced together, one in each half of packed FP32x2
 //    instructions (crkfr_f2.cuh), which halves the instructions of the pair
-//    fluxes.
+//    fluxes;
+//  * the next tile's u^n arrives by TMA bulk copy while the current tile
+//    computes (persistent CTAs, one mbarrier, bounded waits);
+//  * the register budget (resident CTAs per SM) is set per variant from
+//    measurements; the batched form compiles a second shape and lets its
+//    autotuner choose.
 #pragma once
 #include <type_traits>
 
