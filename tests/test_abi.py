@@ -63,3 +63,44 @@ def test_descriptor_layout_matches_c(tmp_path):
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     D = crkfr.MeshDesc
     assert got == [ctypes.sizeof(D), D.lo.offset, D.gamma.offset, D.dt_fixed.offset, D.prec.offset]
+
+
+def _init_status(lib, mesh, prec="fp64"):
+    from paper_2604_02125_gb300 import crkfr
+    d = crkfr.make_desc(mesh, prec)
+    h = ctypes.c_void_p()
+    return lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d), 1, None)
+
+
+def test_invalid_descriptors_rejected_without_gpu(lib):
+    """Descriptor validation runs before any CUDA call, so every malformed or
+    unsupported descriptor is CR_EINVAL on any machine."""
+    from paper_2604_02125_gb300 import crkfr, inputs
+    base = inputs.mesh_dict("euler", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 1.4)
+    bad = [dict(base, N=0), dict(base, N=6), dict(base, dim=0), dict(base, dim=4), dict(base, cells=[0, 4]),
+           dict(base, hi=[0.0, 1.0]), dict(base, gamma=1.0), dict(base, cfl=0.0),
+           dict(base, cells=[32768, 32768], N=1),                  # 2^32 nodes: beyond 32-bit node indices
+           dict(base, eq="glm_mhd", dim=3, cells=[2, 2, 2]), dict(base, eq="glm_mhd", vol="kep")]
+    for m in bad:
+        assert _init_status(lib, m) == crkfr.CR_EINVAL, m
+    d = crkfr.make_desc(base)
+    h = ctypes.c_void_p()
+    for field, value in (("surf", 1), ("prec", 2), ("vol", 3), ("dt_fixed", -1.0)):
+        d2 = crkfr.make_desc(base)
+        setattr(d2, field, value)
+        assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL, field
+    assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d), 0, None) == crkfr.CR_EINVAL
+
+
+def test_noalloc_size_limit_without_gpu(lib):
+    """cr_step_noalloc rejects a mesh whose scratch exceeds its static array
+    (CR_ETOOLARGE) and a malformed descriptor (CR_EINVAL) before any CUDA
+    call; the state pointers are not touched on those paths."""
+    from paper_2604_02125_gb300 import crkfr, inputs
+    big = crkfr.make_desc(inputs.mesh_dict("euler", 2, 3, [128, 128], [0, 0], [1.0, 1.0], 1.4))
+    dummy = ctypes.c_void_p(256)
+    assert lib.cr_step_noalloc(ctypes.byref(big), dummy, dummy, None, None) == crkfr.CR_ETOOLARGE
+    bad = crkfr.make_desc(inputs.mesh_dict("euler", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 1.4))
+    bad.degree_N = 9
+    assert lib.cr_step_noalloc(ctypes.byref(bad), dummy, dummy, None, None) == crkfr.CR_EINVAL
+    assert lib.cr_step_noalloc(None, dummy, dummy, None, None) == crkfr.CR_EINVAL
