@@ -220,3 +220,58 @@ def test_step_elements_equals_full_step(orc, case):
     assert np.array_equal(part, full[:, sel, :])
     with pytest.raises(ValueError):
         orc.step_elements(mesh, U, dt, [E])
+
+
+@pytest.mark.parametrize("eq,dim", [("euler", 1), ("euler", 2), ("euler", 3), ("glm_mhd", 2)])
+def test_cfl_dt_closed_form(orc, eq, dim):
+    """dt = CFL / (sum_d lambda_d / dx_d) on a constant state, with lambda_d =
+    |v_d| + c (Euler, c^2 = gamma p / rho) or |v_d| + max(c_f,d, c_h) (GLM-MHD,
+    fast magnetosonic speed along d), written out here from the wave speeds."""
+    cells = [5, 3, 4][:dim]
+    hi = [1.0, 2.0, 0.5][:dim]
+    mesh = inputs.mesh_dict(eq, dim, 3, cells, [0.0] * dim, hi, 1.4 if eq == "euler" else 5.0 / 3.0,
+                            cfl=0.1, c_h=0.3 if eq == "glm_mhd" else 0.0)
+    U = _const_state(mesh)
+    u = U[:, 0, 0]
+    g = mesh["gamma"]
+    rho = u[0]
+    if eq == "euler":
+        v = u[1:1 + dim] / rho
+        p = (g - 1) * (u[dim + 1] - 0.5 * rho * v @ v)
+        lam = [abs(v[d]) + np.sqrt(g * p / rho) for d in range(dim)]
+    else:
+        v, B, psi = u[1:4] / rho, u[5:8], u[8]
+        p = (g - 1) * (u[4] - 0.5 * rho * v @ v - 0.5 * B @ B - 0.5 * psi ** 2)
+        a2, b2 = g * p / rho, B @ B / rho
+        lam = []
+        for d in range(dim):
+            cf = np.sqrt(0.5 * (a2 + b2 + np.sqrt((a2 + b2) ** 2 - 4 * a2 * B[d] ** 2 / rho)))
+            lam.append(abs(v[d]) + max(cf, mesh["c_h"]))
+    dx = [hi[d] / cells[d] for d in range(dim)]
+    expect = 0.1 / sum(lam[d] / dx[d] for d in range(dim))
+    assert abs(orc.cfl_dt(mesh, U) - expect) <= 1e-14 * expect
+
+
+def test_energy_entropy_totals_quadrature(orc):
+    """totals[M] = sum w |m|^2 / (2 rho) and totals[M+1] = sum w (-rho s/(gamma-1)),
+    s = ln p - gamma ln rho, by GLL quadrature written out here, on a
+    non-constant state (and on a constant state against volume x density)."""
+    mesh, U = inputs.shear_layer_2d(cells=(5, 4), N=3)
+    W = _weights(mesh, orc)
+    vol = np.prod([(mesh["hi"][k] - mesh["lo"][k]) / mesh["cells"][k] for k in range(2)])
+    g = mesh["gamma"]
+    rho, m, E = U[0], U[1:3], U[3]
+    ke = 0.5 * (m ** 2).sum(axis=0) / rho
+    p = (g - 1) * (E - ke)
+    S = -rho * (np.log(p) - g * np.log(rho)) / (g - 1)
+    tot = orc.totals(mesh, U)
+    np.testing.assert_allclose(tot[4], vol * np.einsum("ep,p->", ke, W), rtol=1e-13)
+    np.testing.assert_allclose(tot[5], vol * np.einsum("ep,p->", S, W), rtol=1e-13)
+    Uc = _const_state(mesh)
+    u = Uc[:, 0, 0]
+    area = 2.0 * 2.0
+    kec = 0.5 * (u[1] ** 2 + u[2] ** 2) / u[0]
+    pc = (g - 1) * (u[3] - kec)
+    tc = orc.totals(mesh, Uc)
+    np.testing.assert_allclose(tc[4], area * kec, rtol=1e-13)
+    np.testing.assert_allclose(tc[5], area * (-u[0] * (np.log(pc) - g * np.log(u[0])) / (g - 1)), rtol=1e-13)
