@@ -24,7 +24,10 @@
  *     communication non-conservative numerical flux B(u^{n,+-}) g^avg(U)
  *     (Sec. 2.3, the variant used for all of the paper's results),
  *   - final update (eqs. crkfr.non.cons.final, total.F.non.cons) with the
- *     flux-differencing time-averaged volume term (Sec. 3).
+ *     flux-differencing time-averaged volume term (Sec. 3);
+ *   - the multi-stage RKFR step the cRKFR method is derived from (eq.
+ *     rkfr.non.cons): the same RK tableau on the semi-discrete FR system,
+ *     one face exchange per stage (or_rkfr_step).
  *
  * Readings of points the paper leaves open:
  *   - multi-D: tensor product, sum of per-direction 1D operators on a
@@ -798,6 +801,42 @@ int or_fr_rhs(const or_desc *d, const double *Un, double *RHS) {
   }
   free(un);
   return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Multi-stage RKFR step (eqs. rkfr1, rkfr2): the degree's explicit RK method
+ * (or_butcher) applied to the semi-discrete FR system (eq.
+ * general.non.conservative.fr.one) with the Rusanov surface flux.  With
+ * L(u) = -(local derivative + face corrections) = or_fr_rhs(u):
+ *   u^(i)   = u^n + dt sum_{j<i} a_ij L(u^(j)),  i = 1..s,
+ *   u^{n+1} = u^n + dt sum_j   b_j  L(u^(j)).
+ * Every stage evaluates the numerical fluxes of its own face traces u^(j,+-)
+ * (s inter-element exchanges per step, against one for cRKFR).              */
+/* ------------------------------------------------------------------------- */
+int or_rkfr_step(const or_desc *d, const double *Un, double dt, double *Unew) {
+  or_mesh m;
+  if (d->surf != 0 || mesh_setup(d, &m)) return -1;
+  size_t tot = (size_t)m.M * m.E * m.np;
+  double *K = malloc(sizeof(double) * tot * m.S);
+  double *us = malloc(sizeof(double) * tot);
+  int rc = 0;
+  for (int i = 0; i < m.S && rc == 0; ++i) {
+    for (size_t k = 0; k < tot; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < i; ++j) acc += m.A[i][j] * K[j * tot + k];
+      us[k] = Un[k] + dt * acc;
+    }
+    rc = or_fr_rhs(d, us, &K[i * tot]);
+  }
+  if (rc == 0)
+    for (size_t k = 0; k < tot; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < m.S; ++j) acc += m.b[j] * K[j * tot + k];
+      Unew[k] = Un[k] + dt * acc;
+    }
+  free(K);
+  free(us);
+  return rc;
 }
 
 /* ------------------------------------------------------------------------- */

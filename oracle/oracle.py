@@ -70,6 +70,7 @@ def lib():
         _lib.or_element_stages.argtypes = [P, D, ctypes.c_double, D, D, D, D]
         _lib.or_local_residual.argtypes = [P, D, D]
         _lib.or_fr_rhs.argtypes = [P, D, D]
+        _lib.or_rkfr_step.argtypes = [P, D, ctypes.c_double, D]
         _lib.or_totals.argtypes = [P, D, D]
     return _lib
 
@@ -201,6 +202,28 @@ def run(mesh, U, nsteps, dt_fixed=None):
     for _ in range(nsteps):
         dt = dt_fixed if dt_fixed is not None else cfl_dt(mesh, U)
         U = step(mesh, U, dt)
+        dts.append(dt)
+    return U, dts
+
+
+def rkfr_step(mesh, U, dt):
+    """One multi-stage RKFR step (eq. rkfr.non.cons: the degree's RK tableau on
+    the semi-discrete FR system, one face exchange per stage) with the given
+    dt; U is [var][elem][node] FP64."""
+    d = make_desc(mesh)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    if lib().or_rkfr_step(ctypes.byref(d), _ptr(U), float(dt), _ptr(out)):
+        raise ValueError("oracle rejected the mesh descriptor")
+    return out
+
+
+def rkfr_run(mesh, U, nsteps, dt_fixed=None):
+    """nsteps RKFR steps, dt as in run().  Returns (U, list of dt)."""
+    dts = []
+    for _ in range(nsteps):
+        dt = dt_fixed if dt_fixed is not None else cfl_dt(mesh, U)
+        U = rkfr_step(mesh, U, dt)
         dts.append(dt)
     return U, dts
 
