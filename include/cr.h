@@ -56,6 +56,14 @@ extern "C" {
 /* surface flux (eq. numflux.cons) */
 #define CR_SURF_RUSANOV 0
 
+/* time stepping scheme */
+#define CR_SCHEME_CRKFR 0      /* compact RKFR (eqs. crkfr.inner, crkfr.non.cons.final): element-local
+                                  stages, one face exchange per step -- the paper's method      */
+#define CR_SCHEME_RKFR  1      /* multi-stage RKFR (eq. rkfr.non.cons), the scheme cRKFR is derived
+                                  from: the same RK tableau on the semi-discrete FR system, a
+                                  face exchange (Rusanov flux of the stage traces) at every
+                                  stage; for measuring the single-stage advantage                */
+
 /* arithmetic of the element-local work */
 #define CR_FP64          0     /* every step of the path in FP64                        */
 #define CR_FP32_PAIRFLUX 1     /* stages, pair fluxes, time averages and face fluxes in
@@ -75,6 +83,8 @@ typedef struct {
   int vol;           /* CR_VOL_*                                                        */
   int surf;          /* CR_SURF_RUSANOV                                                 */
   int prec;          /* CR_FP64 | CR_FP32_PAIRFLUX                                      */
+  int scheme;        /* CR_SCHEME_CRKFR (0) | CR_SCHEME_RKFR; the batched form and
+                        cr_step_noalloc take CR_SCHEME_CRKFR only                        */
 } cr_mesh_desc;
 
 typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
@@ -83,7 +93,9 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  *   out        : receives the context (NULL on failure).
  *   desc       : n_solves descriptors (copied).
  *   n_solves   : 1 = one mesh advanced by two kernels per step (volume, face +
- *                update, replayed as a CUDA graph); > 1 = batched form: the
+ *                update, replayed as a CUDA graph; CR_SCHEME_RKFR: the two
+ *                kernels once per RK stage, the volume kernel on the stage
+ *                state with a single stage); > 1 = batched form: the
  *                solves (meshes and degrees may differ) advance together, per
  *                step one persistent volume kernel and one persistent face /
  *                update kernel per degree present, all replayed from one CUDA
@@ -92,7 +104,8 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  *                prec and vol for all solves (and the same gamma per degree).
  *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
  * The library allocates and owns all device buffers (state, stage/trace
- * scratch, step records).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+ * scratch, step records; CR_SCHEME_RKFR adds a stage state and s - 1 stage
+ * increments).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
 /* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */
@@ -143,7 +156,8 @@ int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps,
  * are overwritten (cudaMemsetAsync) to evict the L2.  ms[0] receives the mean
  * duration of one volume-kernel launch, ms[1] of one face/update launch (the
  * batched form: ms[0] = the volume launches of all degrees of one step, ms[1]
- * = their face/update launches).  The state advances exactly as with
+ * = their face/update launches; CR_SCHEME_RKFR: ms[0] = the s volume
+ * launches of one step, ms[1] = its s face/update launches).  The state advances exactly as with
  * cr_step.  Synchronises the stream. */
 int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
 
@@ -181,7 +195,8 @@ int cr_check_conversions(long long n, unsigned long long seed, long long *mismat
  *   u_out      : device pointer, receives u^{n+1}; may equal u_in.
  *   dt_out     : device pointer receiving the dt used (FP64), or NULL.
  *   cuda_stream: stream for all work (asynchronous; nothing is synchronised).
- * dt follows the descriptor (CFL rule on u^n, or dt_fixed).  The scratch
+ * dt follows the descriptor (CFL rule on u^n, or dt_fixed); desc->scheme must
+ * be CR_SCHEME_CRKFR (CR_EINVAL otherwise).  The scratch
  * (residual sums, face traces, reductions, step record) lives in one static
  * device array of CR_NOALLOC_SCRATCH_BYTES per device, held until the
  * process exits; a mesh needing more returns CR_ETOOLARGE (roughly 80k nodes

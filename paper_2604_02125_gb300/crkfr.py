@@ -19,6 +19,7 @@ EQ = {"euler": 0, "glm_mhd": 1}
 VOL = {"ec": 0, "kep": 1, "central": 2}
 SURF = {"rusanov": 0}
 PREC = {"fp64": 0, "fp32": 1}
+SCHEME = {"crkfr": 0, "rkfr": 1}
 
 
 class CrError(RuntimeError):
@@ -32,7 +33,7 @@ class MeshDesc(ctypes.Structure):
                 ("cells", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("vol", ctypes.c_int), ("surf", ctypes.c_int),
-                ("prec", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 _lib = None
@@ -84,7 +85,9 @@ def status_string(s):
         return "status %d" % s
 
 
-def make_desc(mesh, prec="fp64", dt_fixed=0.0):
+def make_desc(mesh, prec="fp64", dt_fixed=0.0, scheme=None):
+    """Descriptor of a mesh dict; scheme ('crkfr' or 'rkfr', the multi-stage
+    scheme) defaults to the dict's 'scheme' key, else 'crkfr'."""
     d = MeshDesc()
     d.eq = EQ[mesh.get("eq", "euler")]
     d.dim = mesh["dim"]
@@ -101,6 +104,7 @@ def make_desc(mesh, prec="fp64", dt_fixed=0.0):
     d.vol = VOL[mesh.get("vol", "ec")]
     d.surf = SURF[mesh.get("surf", "rusanov")]
     d.prec = PREC[prec]
+    d.scheme = SCHEME[scheme or mesh.get("scheme", "crkfr")]
     return d
 
 
@@ -125,15 +129,18 @@ class Solver:
     """One mesh (mesh dict) or a batch of meshes (list of mesh dicts).
 
     prec: 'fp64' (plain path) or 'fp32' (FP32 pair fluxes, FP64 update).
+    scheme: 'crkfr' (the single-stage method) or 'rkfr' (the multi-stage
+    scheme it is derived from, one face exchange per RK stage; one mesh only);
+    default: each mesh dict's 'scheme' key, else 'crkfr'.
     stream: a cudaStream_t handle (int) or a torch.cuda.Stream; default: the
     current torch stream if torch has initialised CUDA, else the legacy stream.
     """
 
-    def __init__(self, mesh, prec="fp64", dt_fixed=0.0, stream=None):
+    def __init__(self, mesh, prec="fp64", dt_fixed=0.0, stream=None, scheme=None):
         self.lib = load_library()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         self.meshes = list(meshes)
-        arr = (MeshDesc * len(meshes))(*[make_desc(m, prec, dt_fixed) for m in meshes])
+        arr = (MeshDesc * len(meshes))(*[make_desc(m, prec, dt_fixed, scheme) for m in meshes])
         self._descs = arr
         if stream is None:
             stream = _current_torch_stream()

@@ -2,8 +2,9 @@
 //
 // One solve (n_solves == 1): per step the volume kernel and the fused
 // face-flux/update kernel run on the caller's stream, replayed from CUDA graphs
-// captured at set-up (1-step and 16-step graphs).  The batched form
-// (n_solves > 1) lives in cr_batched.cu.
+// captured at set-up (1-step and 16-step graphs); the multi-stage RKFR scheme
+// runs the pair once per RK stage.  The batched form (n_solves > 1) lives in
+// cr_batched.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -242,6 +243,7 @@ static bool desc_valid(const cr_mesh_desc& d) {
   if (d.degree_N < 1 || d.degree_N > 5) return false;
   if (d.vol < 0 || d.vol > 2 || d.surf != CR_SURF_RUSANOV) return false;
   if (d.prec != CR_FP64 && d.prec != CR_FP32_PAIRFLUX) return false;
+  if (d.scheme != CR_SCHEME_CRKFR && d.scheme != CR_SCHEME_RKFR) return false;
   if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || d.dt_fixed < 0.0 || !(d.c_h >= 0.0)) return false;
   for (int k = 0; k < d.dim; ++k) {
     if (d.cells[k] < 1) return false;
@@ -262,12 +264,24 @@ static void free_single(cr_ctx* c) {
   cudaFree(c->lc.trace);
   cudaFree(c->lc.st);
   cudaFree(c->lc.totals_part);
+  cudaFree(c->lc.ustage);
+  cudaFree(c->lc.kbuf);
   c->cap_stream = nullptr;
 }
 
 // one step from the state whose CFL reduction sits in slot `parity`
 static int launch_step(cr_ctx* c, cudaStream_t s, int parity) {
   c->lc.slot = parity;
+  if (c->desc[0].scheme == CR_SCHEME_RKFR) {
+    // stage j: volume part on u^(j) (u^n for j = 0), face / update part
+    // forming u^(j+1) (the state itself after the last stage)
+    const int S = rk_stages(c->desc[0].degree_N);
+    for (int j = 0; j < S; ++j) {
+      CR_TRY(c->ops.volume_stage(c->lc, s, j == 0 ? c->lc.u : c->lc.ustage, j == 0));
+      CR_TRY(c->ops.face_stage(c->lc, s, j, S));
+    }
+    return CR_OK;
+  }
   CR_TRY(c->ops.volume(c->lc, s));
   CR_TRY(c->ops.face_update(c->lc, s));
   return CR_OK;
@@ -312,6 +326,10 @@ static int init_single(cr_ctx* c) {
   al(&lc.trace, o.real_bytes * (size_t)o.dim * 2 * o.C * NFt);
   al((void**)&lc.st, sizeof(DevState));
   al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
+  if (d.scheme == CR_SCHEME_RKFR) {
+    al((void**)&lc.ustage, sizeof(double) * (size_t)o.M * nodes);
+    al(&lc.kbuf, o.real_bytes * (size_t)(rk_stages(d.degree_N) - 1) * o.M * nodes);
+  }
   if (rc != CR_OK) { free_single(c); return rc; }
   lc.ma.tma_ok = tma_ok_for(lc.u, E, o.NP);
   cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
@@ -473,7 +491,10 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
   if (!c || nsteps < 1 || !ms) return CR_EINVAL;
   if (c->batched) return batched_time_kernels(c->batched, nsteps, flush_buf, flush_bytes, ms);
   if (!c->has_state) return CR_EINVAL;
-  std::vector<cudaEvent_t> ev(4 * (size_t)nsteps, nullptr);
+  // launches per step of each kind: 1, or one per RK stage (multi-stage RKFR)
+  const bool rk = c->desc[0].scheme == CR_SCHEME_RKFR;
+  const int S = rk ? rk_stages(c->desc[0].degree_N) : 1;
+  std::vector<cudaEvent_t> ev(4 * (size_t)nsteps * S, nullptr);
   int rc = CR_OK;
   for (auto& e : ev)
     if (rc == CR_OK && cudaEventCreate(&e) != cudaSuccess) rc = CR_ECUDA;
@@ -482,18 +503,26 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
       rc = CR_ECUDA;
       break;
     }
-    cudaEventRecord(ev[4 * k + 0], c->stream);
     c->lc.slot = c->parity;
-    if (c->ops.volume(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
-    cudaEventRecord(ev[4 * k + 1], c->stream);
-    cudaEventRecord(ev[4 * k + 2], c->stream);
-    if (rc == CR_OK && c->ops.face_update(c->lc, c->stream) != cudaSuccess) rc = CR_ECUDA;
-    cudaEventRecord(ev[4 * k + 3], c->stream);
+    for (int j = 0; j < S && rc == CR_OK; ++j) {
+      cudaEvent_t* e4 = &ev[4 * ((size_t)k * S + j)];
+      cudaEventRecord(e4[0], c->stream);
+      cudaError_t e = rk ? c->ops.volume_stage(c->lc, c->stream, j == 0 ? c->lc.u : c->lc.ustage, j == 0)
+                         : c->ops.volume(c->lc, c->stream);
+      if (e != cudaSuccess) rc = CR_ECUDA;
+      cudaEventRecord(e4[1], c->stream);
+      cudaEventRecord(e4[2], c->stream);
+      if (rc == CR_OK) {
+        e = rk ? c->ops.face_stage(c->lc, c->stream, j, S) : c->ops.face_update(c->lc, c->stream);
+        if (e != cudaSuccess) rc = CR_ECUDA;
+      }
+      cudaEventRecord(e4[3], c->stream);
+    }
     if (rc == CR_OK) c->parity ^= 1;
   }
   if (rc == CR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CR_ECUDA;
   double tv = 0.0, tf = 0.0;
-  for (int k = 0; k < nsteps && rc == CR_OK; ++k) {
+  for (size_t k = 0; k < (size_t)nsteps * S && rc == CR_OK; ++k) {
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]);
     cudaEventElapsedTime(&b, ev[4 * k + 2], ev[4 * k + 3]);
@@ -525,9 +554,10 @@ int cr_tuning_info(cr_ctx* c, char* buf, size_t len) {
     info = batched_tuning(c->batched);
   } else {
     char tmp[256];
-    std::snprintf(tmp, sizeof(tmp), "{\"volume\": \"%s\", \"elements_per_cta\": %d, \"face\": \"%s\"}",
-                  c->ops.lanes ? "lanes" : "tile", c->ops.lanes ? 32 : c->lc.epb,
-                  c->ops.threads_face > 0 ? "lanes" : "per-node");
+    std::snprintf(tmp, sizeof(tmp),
+                  "{\"scheme\": \"%s\", \"volume\": \"%s\", \"elements_per_cta\": %d, \"face\": \"%s\"}",
+                  c->desc[0].scheme == CR_SCHEME_RKFR ? "rkfr" : "crkfr", c->ops.lanes ? "lanes" : "tile",
+                  c->ops.lanes ? 32 : c->lc.epb, c->ops.threads_face > 0 ? "lanes" : "per-node");
     info = tmp;
   }
   std::snprintf(buf, len, "%s", info.c_str());

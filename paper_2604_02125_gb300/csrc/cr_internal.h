@@ -22,6 +22,10 @@ struct LaunchCtx {
   int epb;            // elements per CTA of the volume kernel (tile form)
   int sms;            // multiprocessors of the device (persistent grids)
   int slot;           // step parity: CFL-reduction slot of the state the next step starts from
+  // multi-stage RKFR scratch: stage state u^(j) (FP64, like u) and the
+  // increments K_0..K_{s-2} ([stage][var][elem][node], R)
+  double* ustage;
+  void* kbuf;
 };
 
 // One launch of a batched persistent kernel (all solves of one degree).
@@ -46,6 +50,11 @@ struct VariantOps {
   size_t real_bytes;           // sizeof(R)
   cudaError_t (*volume)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*face_update)(const LaunchCtx&, cudaStream_t);
+  // one stage of the multi-stage RKFR step: volume part on u_in (first: the
+  // step's first launch, which derives and records dt), face / update part of
+  // stage j of s (intermediate stage states go to ustage, the last to u)
+  cudaError_t (*volume_stage)(const LaunchCtx&, cudaStream_t, const double* u_in, int first);
+  cudaError_t (*face_stage)(const LaunchCtx&, cudaStream_t, int j, int s);
   cudaError_t (*lambda)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*totals)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*set_smem)(size_t bytes);

@@ -62,8 +62,50 @@ struct Variant {
     }
     return cudaGetLastError();
   }
+  static cudaError_t volume_stage(const LaunchCtx& c, cudaStream_t s, const double* u_in, int first) {
+    if constexpr (kLanes) {
+      const long long ntiles = (c.ma.E + 31) / 32;
+      const long long grid = std::min(ntiles, (long long)c.sms * vol_stage_occupancy());
+      k_volume_lanes_stage<EQ, N, R><<<(unsigned)grid, LL::THREADS, PL::bytes(), s>>>(
+          u_in, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot, first);
+    } else {
+      const long long grid = (c.ma.E + c.epb - 1) / c.epb;
+      const int threads = c.epb * L::NF;
+      const size_t smem = (size_t)c.epb * L::bytes_per_elem();
+      k_volume_tile_stage<EQ, N, R><<<(unsigned)grid, threads, smem, s>>>(
+          u_in, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot, first);
+    }
+    return cudaGetLastError();
+  }
+  static int vol_stage_occupancy() {
+    static int occ = -1;
+    if (occ < 0) {
+      int nb = 0;
+      if constexpr (kLanes) {
+        cudaFuncSetAttribute(k_volume_lanes_stage<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_lanes_stage<EQ, N, R>, LL::THREADS, PL::bytes());
+      }
+      occ = nb > 0 ? nb : 1;
+    }
+    return occ;
+  }
   using FL = FaceLaneLayout<EQ, N, R>;
   static constexpr bool kFaceLanes = FL::fits();
+  static cudaError_t face_stage(const LaunchCtx& c, cudaStream_t s, int j, int ns) {
+    const RkStage<R> rk{(R*)c.kbuf, j == ns - 1 ? c.u : c.ustage, j, ns};
+    if constexpr (kFaceLanes) {
+      const unsigned grid = (unsigned)((c.ma.E + 31) / 32);
+      k_face_stage_lanes<EQ, N, R><<<grid, FL::THREADS, FL::bytes(), s>>>(
+          c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot, rk);
+    } else {
+      const long long total = c.ma.E * L::NP;
+      const unsigned grid = (unsigned)((total + 255) / 256);
+      k_face_stage<EQ, N, R><<<grid, 256, 0, s>>>(c.u, (const R*)c.rbar, (const R*)c.trace, c.st, c.ma,
+                                                   PP<R>::get(c), PP<R>::tab(c), c.slot, rk);
+    }
+    return cudaGetLastError();
+  }
   static constexpr bool kBatched = EQ::DIM == 2 && !EQ::NC && kLanes && kFaceLanes;
   static cudaError_t face_update(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (kFaceLanes) {
@@ -95,6 +137,9 @@ struct Variant {
       cudaError_t e = cudaFuncSetAttribute(k_face_update_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)FL::bytes());
       if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_face_stage_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)FL::bytes());
+      if (e != cudaSuccess) return e;
       if constexpr (kBatched) {
         e = cudaFuncSetAttribute(k_face_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)FL::bytes());
@@ -110,10 +155,16 @@ struct Variant {
                                  (int)PL::bytes());
         if (e != cudaSuccess) return e;
       }
+      cudaError_t e = cudaFuncSetAttribute(k_volume_lanes_stage<EQ, N, R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_volume_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    }
-    else
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(k_volume_tile_stage<EQ, N, R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_volume_tile<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
   }
   static cudaError_t vol_batched(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (kBatched) {
@@ -154,7 +205,7 @@ struct Variant {
     o->occupancy = kBatched ? &occupancy : nullptr;
     o->vol_shapes = kBatched ? 2 : 0;
     o->threads_vol = LL::THREADS;
-    o->threads_face = FL::THREADS;
+    o->threads_face = kFaceLanes ? FL::THREADS : 0;
     o->M = EQ::M;
     o->NP = L::NP;
     o->NF = L::NF;
@@ -166,6 +217,8 @@ struct Variant {
     o->real_bytes = sizeof(R);
     o->volume = &volume;
     o->face_update = &face_update;
+    o->volume_stage = &volume_stage;
+    o->face_stage = &face_stage;
     o->lambda = &lambda;
     o->totals = &totals;
     o->set_smem = &set_smem;

@@ -100,6 +100,19 @@ struct DevState {
 
 constexpr unsigned ST_NONPHYS = 1u, ST_TIMEOUT = 2u;
 
+// One stage of the multi-stage RKFR step (eq. rkfr.non.cons), for the face /
+// update kernels in stage mode.  Stage j (0-based) of s forms the increment
+// K_j = -dt R_FR(u^(j)) at every node and combines it with the earlier ones:
+// u^(j+1) = u^n + sum_{q<=j} a_{j+1,q} K_q into uout, or, at the last stage,
+// u^{n+1} = u^n + sum_q b_q K_q into the state (followed by the CFL
+// reduction).  k holds K_0..K_{s-2}, [stage][var][elem][node].
+template <typename R>
+struct RkStage {
+  R* k;
+  double* uout;
+  int j, s;
+};
+
 // ---------------------------------------------------------------------------
 // CFL reduction: every warp takes its maximum with shuffles and folds it into
 // lam_bits[slot] with one 64-bit atomicMax (non-negative doubles order like
@@ -199,12 +212,15 @@ __device__ __forceinline__ unsigned neighbour_of(unsigned e, const unsigned (&c)
 // Volume kernel, tile form: one CTA holds epb elements; one thread per line.
 // Used where the lane form below does not fit in shared memory.
 // ---------------------------------------------------------------------------
-template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(256)
-k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
-         DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, int slot) {
+// S1 = 1: a single stage with b = 1 (R-bar = R(u), face records of u), the
+// volume part of one stage of the multi-stage RKFR step; first = false takes
+// the dt the step's first launch recorded.
+template <class EQ, int N, typename R, int S1>
+__device__ __forceinline__ void volume_tile_body(const double* __restrict__ u, R* __restrict__ rbar,
+                                                 R* __restrict__ trace, DevState* __restrict__ st, const MeshArgs& ma,
+                                                 const PhysParams<R>& pp, const RefTab<R>& tb, int slot, bool first) {
   using L = VolLayout<EQ, N, R>;
-  constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
+  constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = S1 ? S1 : L::S;
   constexpr int C = trace_comps<EQ>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sm = reinterpret_cast<R*>(smem_raw);
@@ -220,7 +236,7 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
   R* my = sm + (size_t)el * L::SZ;
 
   __shared__ double s_dt;
-  if (tid == 0) s_dt = step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0);
+  if (tid == 0) s_dt = first ? step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0) : st->dt;
   __syncthreads();
   const R dtR = dt_as<R>(s_dt);
 
@@ -266,7 +282,7 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
           for (int d = 0; d < DIM; ++d)
             if (cd[d] == 0 || cd[d] == N) my[L::O_LAM + d * NP + p] = EQ::wave_speed(d, q, pp);
         }
-        const double bi = rk_b(N, i);
+        const double bi = S1 ? 1.0 : rk_b(N, i);
         if (bi != 0.0 && onface) {
           const R b = R(bi);
 #pragma unroll
@@ -376,7 +392,7 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
       R s = R(0);
 #pragma unroll
       for (int i = 0; i < S; ++i)
-        if (rk_b(N, i) != 0.0) s += R(rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
+        if ((S1 ? 1.0 : rk_b(N, i)) != 0.0) s += R(S1 ? 1.0 : rk_b(N, i)) * mm[L::O_RS + (i * M + v) * NP + p];
       rbar[((size_t)v * E + e0) * NP + r] = s;
     }
   // face traces: per face node C components (coalesced over the elements)
@@ -399,6 +415,22 @@ k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict_
     else val = mm[L::O_U0 + (c - 3 * M - 1) * NP + p];
     trace[trace_index<EQ, NF>(d, side, f, c, E, e0 + ee)] = val;
   }
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_volume_tile(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+         DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, int slot) {
+  volume_tile_body<EQ, N, R, 0>(u, rbar, trace, st, ma, pp, tb, slot, true);
+}
+
+// volume part of one RKFR stage (input: the stage state)
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_volume_tile_stage(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+                    DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                    int slot, int first) {
+  volume_tile_body<EQ, N, R, 1>(u, rbar, trace, st, ma, pp, tb, slot, first != 0);
 }
 
 // physicality and sum_d lambda_d/dx_d of an updated state; the FP32 form
@@ -466,11 +498,12 @@ __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long
   jump_of<EQ, R>(o, x, d, side_own, J, pp);
 }
 
-template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(256)
-k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
-              DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
-              int slot) {
+// RK = true: stage mode of the multi-stage RKFR step (RkStage)
+template <class EQ, int N, typename R, bool RK>
+__device__ __forceinline__ void face_update_body(double* __restrict__ u, const R* __restrict__ rbar,
+                                                 const R* __restrict__ trace, DevState* __restrict__ st,
+                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
+                                                 int slot, const RkStage<R>& rk) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM);
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
@@ -512,6 +545,27 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
         for (int v = 0; v < M; ++v) du[v] += s * J[v];
       }
     }
+    bool last = true;
+    double* dst = u;
+    if constexpr (RK) {
+      // du is this stage's K_j; combine it with the earlier stages' (eq. rkfr1
+      // for the next stage state, eq. rkfr2 at the last stage)
+      last = rk.j == rk.s - 1;
+      const size_t nodes = (size_t)E * NP;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const size_t g = ((size_t)v * E + e) * NP + p;
+        const R kj = du[v];
+        if (!last) rk.k[(size_t)rk.j * M * nodes + g] = kj;
+        R acc = (last ? tb.b[rk.j] : tb.a[rk.j + 1][rk.j]) * kj;
+        for (int q = 0; q < rk.j; ++q) {
+          const R c = last ? tb.b[q] : tb.a[rk.j + 1][q];
+          if (c != R(0)) acc += c * rk.k[(size_t)q * M * nodes + g];
+        }
+        du[v] = acc;
+      }
+      if (!last) dst = rk.uout;
+    }
     // u^{n+1} = u^n + du in FP64 (one FP64 add per variable)
     double uu[M];
 #pragma unroll
@@ -519,11 +573,30 @@ k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __res
       const size_t g = ((size_t)v * E + e) * NP + p;
       if constexpr (F32) uu[v] = u[g] + f2d_int(du[v]);
       else uu[v] = u[g] + du[v];
-      u[g] = uu[v];
+      dst[g] = uu[v];
     }
-    bad = !physical_state<EQ, R>(uu, ma, lam);
+    if (last) bad = !physical_state<EQ, R>(uu, ma, lam);
   }
-  reduce_lambda<R>(lam, bad, st, slot ^ 1);
+  // the CFL reduction of the new state (RKFR: after the last stage only; the
+  // stage index is uniform over the grid)
+  if (!RK || rk.j == rk.s - 1) reduce_lambda<R>(lam, bad, st, slot ^ 1);
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_face_update(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+              DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+              int slot) {
+  face_update_body<EQ, N, R, false>(u, rbar, trace, st, ma, pp, tb, slot, RkStage<R>{nullptr, nullptr, 0, 1});
+}
+
+// face / update part of stage rk.j of the multi-stage RKFR step
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_face_stage(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+             DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+             int slot, const RkStage<R> rk) {
+  face_update_body<EQ, N, R, true>(u, rbar, trace, st, ma, pp, tb, slot, rk);
 }
 
 // CFL reduction of the current state (used after set_state); wave speeds in

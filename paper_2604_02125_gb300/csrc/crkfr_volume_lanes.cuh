@@ -300,15 +300,17 @@ __device__ __forceinline__ void issue_prefetch(const Prefetch& pf) {
 
 // One tile of 32 elements starting at e0 (the CTA's whole shared memory sm).
 // staged != nullptr: u^n of the tile already sits in shared memory as FP64,
-// [var][32][NP] (the tile's slice of the global layout).
-template <class EQ, int N, typename R, int SH = 0>
+// [var][32][NP] (the tile's slice of the global layout).  S1 = 1: a single
+// stage with b = 1 (R-bar = R(u), face records of u), the volume part of one
+// stage of the multi-stage RKFR step.
+template <class EQ, int N, typename R, int SH = 0, int S1 = 0>
 __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
                                                   R* __restrict__ trace, const DevState* __restrict__ st,
                                                   const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
                                                   long long e0, R dtR, R* sm, const double* staged = nullptr,
                                                   Prefetch pf = Prefetch{nullptr, 0, 0, nullptr, nullptr}) {
   using L = LaneLayout<EQ, N, R, SH>;
-  constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = L::S;
+  constexpr int DIM = L::DIM, M = L::M, P = L::P, n = L::n, NP = L::NP, NF = L::NF, S = S1 ? S1 : L::S;
   constexpr int NS = rk_nsaved(N) > 0 ? rk_nsaved(N) : 1;
 
   const int tid = threadIdx.x;
@@ -350,7 +352,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   // would overflow the instruction cache; the tableau comes from the parameters
 #pragma unroll 1
   for (int i = 0; i < S; ++i) {
-    const R bi = tb.b[i];
+    const R bi = S1 ? R(1) : tb.b[i];
     // ---------------- node phase (own x-line): stage state and pair data
     R q[n][P];
     if (active) {
@@ -469,7 +471,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         R r = ax[k][v] + (DIM > 1 ? my[L::O_RY + v * NP + p] : R(0));
-        my[L::O_Q + v * NP + p] = rb[k][v] + tb.b[S - 1] * r;
+        my[L::O_Q + v * NP + p] = rb[k][v] + (S1 ? R(1) : tb.b[S - 1]) * r;
       }
     }
   }
@@ -508,12 +510,14 @@ struct PersistLayout {
 };
 
 // Persistent volume kernel for one solve: CTA b handles tiles b, b + grid, ...;
-// u^n of whole tiles arrives by TMA bulk copy one tile ahead.
-template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
-k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
-               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
-               int slot) {
+// u^n of whole tiles arrives by TMA bulk copy one tile ahead.  first = false
+// (later stages of a multi-stage RKFR step) takes the dt the step's first
+// launch recorded.
+template <class EQ, int N, typename R, int S1>
+__device__ __forceinline__ void volume_lanes_persistent(const double* __restrict__ u, R* __restrict__ rbar,
+                                                        R* __restrict__ trace, DevState* __restrict__ st,
+                                                        const MeshArgs& ma, const PhysParams<R>& pp,
+                                                        const RefTab<R>& tb, int slot, bool first) {
   using PL = PersistLayout<EQ, N, R>;
   constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -529,7 +533,7 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
   __shared__ double s_dt;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    s_dt = step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0);
+    s_dt = first ? step_begin(st, slot, ma.cfl, ma.dt_fixed, blockIdx.x == 0) : st->dt;
   }
   __syncthreads();
   const R dtR = dt_as<R>(s_dt);
@@ -548,10 +552,27 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
     }
     const unsigned tn = t + gridDim.x;
     const Prefetch pf = (tn < ntiles && whole(tn)) ? pf_of(tn) : Prefetch{nullptr, 0, 0, nullptr, nullptr};
-    volume_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
-                                staged ? staging : nullptr, pf);
+    volume_lanes_tile<EQ, N, R, 0, S1>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
+                                       staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }
+}
+
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+               DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+               int slot) {
+  volume_lanes_persistent<EQ, N, R, 0>(u, rbar, trace, st, ma, pp, tb, slot, true);
+}
+
+// volume part of one RKFR stage (input: the stage state)
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+k_volume_lanes_stage(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+                     DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                     int slot, int first) {
+  volume_lanes_persistent<EQ, N, R, 1>(u, rbar, trace, st, ma, pp, tb, slot, first != 0);
 }
 
 }  // namespace crk
@@ -597,6 +618,17 @@ __device__ __forceinline__ void load_line(const T* __restrict__ src, T (&out)[n]
   }
 }
 template <int n>
+__device__ __forceinline__ void store_line(float* __restrict__ dst, const float (&in)[n]) {
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < n / 4; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(in[4 * k], in[4 * k + 1], in[4 * k + 2], in[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < n; ++k) dst[k] = in[k];
+  }
+}
+template <int n>
 __device__ __forceinline__ void store_line(double* __restrict__ dst, const double (&in)[n]) {
   if constexpr (n % 2 == 0) {
 #pragma unroll
@@ -617,11 +649,15 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
 // Phase B: each thread forms the increment of its x-line (eq.
 // crkfr.non.cons.final), the CFL reduction runs, and u^{n+1} is stored last,
 // after the reduction's atomics.
-template <class EQ, int N, typename R>
+// RK = true: stage mode of the multi-stage RKFR step (RkStage): the increment
+// is the stage's K_j, combined with the earlier stages' into the next stage
+// state (eq. rkfr1) or, at the last stage, into u^{n+1} (eq. rkfr2).
+template <class EQ, int N, typename R, bool RK = false>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
-                                                unsigned e0, int slot, R* __restrict__ sj) {
+                                                unsigned e0, int slot, R* __restrict__ sj,
+                                                const RkStage<R>& rk = RkStage<R>{nullptr, nullptr, 0, 1}) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
   constexpr bool F32 = sizeof(R) == 4;
@@ -694,6 +730,33 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
         }
       }
     }
+    if constexpr (RK) {
+      // du is this stage's K_j: keep it for the later stages and combine it
+      // with the earlier ones (a_{j+1,q}, or b_q at the last stage)
+      const bool last = rk.j == rk.s - 1;
+      const size_t nodes = (size_t)E * NP;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const size_t g = ((size_t)v * E + e) * NP + l * n;
+        R kj[n], acc[n];
+        const R cj = last ? tb.b[rk.j] : tb.a[rk.j + 1][rk.j];
+#pragma unroll
+        for (int k = 0; k < n; ++k) { kj[k] = du[k][v]; acc[k] = cj * kj[k]; }
+        if (!last) store_line<n>(rk.k + (size_t)rk.j * M * nodes + g, kj);
+#pragma unroll 1
+        for (int q = 0; q < rk.j; ++q) {
+          const R c = last ? tb.b[q] : tb.a[rk.j + 1][q];
+          if (c != R(0)) {
+            R kq[n];
+            load_line<n>(rk.k + (size_t)q * M * nodes + g, kq);
+#pragma unroll
+            for (int k = 0; k < n; ++k) acc[k] += c * kq[k];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < n; ++k) du[k][v] = acc[k];
+      }
+    }
     // u^{n+1} = u^n + du in FP64
 #pragma unroll
     for (int k = 0; k < n; ++k) {
@@ -704,15 +767,22 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
         else uu[v] = un[v][k] + du[k][v];
         un[v][k] = uu[v];
       }
-      R lk;
-      bad = bad || !physical_state<EQ, R>(uu, ma, lk);
-      lam = fmax(lam, lk);
+      if (!RK || rk.j == rk.s - 1) {
+        R lk;
+        bad = bad || !physical_state<EQ, R>(uu, ma, lk);
+        lam = fmax(lam, lk);
+      }
     }
   }
-  reduce_lambda<R>(lam, bad, st, slot ^ 1);
+  // the CFL reduction of the new state (RKFR: after the last stage only; the
+  // stage index is uniform over the grid); intermediate stage states go to
+  // rk.uout
+  double* dst = u;
+  if (RK && rk.j != rk.s - 1) dst = rk.uout;
+  else reduce_lambda<R>(lam, bad, st, slot ^ 1);
   if (active) {
 #pragma unroll
-    for (int v = 0; v < M; ++v) store_line<n>(u + ((size_t)v * E + e) * NP + l * n, un[v]);
+    for (int v = 0; v < M; ++v) store_line<n>(dst + ((size_t)v * E + e) * NP + l * n, un[v]);
   }
 }
 
@@ -723,6 +793,17 @@ k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R*
                     int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot, reinterpret_cast<R*>(smem_raw));
+}
+
+// face / update part of stage rk.j of the multi-stage RKFR step
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
+k_face_stage_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R* __restrict__ trace,
+                   DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                   int slot, const RkStage<R> rk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  face_lanes_tile<EQ, N, R, true>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot,
+                                  reinterpret_cast<R*>(smem_raw), rk);
 }
 
 // ---------------------------------------------------------------------------

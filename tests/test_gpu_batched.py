@@ -98,6 +98,10 @@ def test_batch_rejects_mixed_forms(cr):
     mh, _ = inputs.mhd_vortex_2d(cells=(4, 4), N=3)
     with pytest.raises(cr.CrError):
         cr.Solver([mh, mh], prec="fp32")
+    # the batched form is the single-stage scheme only
+    with pytest.raises(cr.CrError) as ei:
+        cr.Solver([m for m, _ in batch], prec="fp32", scheme="rkfr")
+    assert ei.value.status == cr.CR_EINVAL
 
 
 def test_batch_step_needs_every_state(cr):
