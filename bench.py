@@ -350,6 +350,21 @@ def main():
 
         batched = None if args.no_batched else run_batched(crkfr, inputs, stream, max(3, min(10, args.steps)))
 
+        # the multi-stage RKFR scheme (eq. rkfr.non.cons) on the same workload
+        # and kernels: s volume and s face exchanges per step, against one
+        # each -- the single-stage advantage the compact scheme is built for
+        rkfr = {}
+        for prec, krk in (("fp32", max(3, min(200, args.steps))), ("fp64", k64)):
+            r = crkfr.Solver(mesh, prec=prec, stream=stream, scheme="rkfr")
+            r.set_state(U)
+            r.step(2)
+            r.sync()
+            trk = time_steps(r, krk, stream, flush)
+            rv, rf = r.time_kernels(max(3, min(20, args.steps)), flush)
+            r.close()
+            rkfr[prec] = {"value": nodes * krk / (sum(trk) * 1e-3), "ms_per_step": sum(trk) / krk, "steps": krk,
+                          "volume_ms_per_step": rv, "face_update_ms_per_step": rf}
+
         # volume-kernel duration, CUDA events on the solver's stream, same L2 flush
         kv = max(3, min(50, args.steps))
         vol_ms, face_ms = s32.time_kernels(kv, flush)
@@ -448,7 +463,13 @@ def main():
                                     "rel_l2_vs_fp64_after_100_steps": err100},
                   "fp64": {"value": nodes * k64 / (sum(t64) * 1e-3), "ms_per_step": sum(t64) / k64, "steps": k64,
                            "rel_l2_vs_oracle_per_step": "<= 1e-12 (tests/test_gpu_parity.py)"},
-                  "batched": batched},
+                  "batched": batched,
+                  "rkfr": dict(rkfr, scheme="multi-stage RKFR, %d stages: per stage one single-stage volume launch "
+                               "and one face/update launch" % stages,
+                               crkfr_speedup={"fp32": rkfr["fp32"]["ms_per_step"] / ms_step,
+                                              "fp64": rkfr["fp64"]["ms_per_step"] / (sum(t64) / k64)},
+                               rel_l2_vs_oracle="<= 1e-12 per step (FP64), <= 1e-5 after 100 steps (FP32): "
+                                                "tests/test_gpu_rkfr.py")},
         "e2e": {"value": world * nodes * ke / e2e_s, "unit": "DOF-updates/s",
                 "h2d_bytes_per_step": int(U.nbytes), "d2h_bytes_per_step": int(U.nbytes),
                 "mode": "per step: full state H2D from pinned memory, one step, full state D2H; 3 contexts "
@@ -462,7 +483,7 @@ def main():
                 "sequential": {"value": world * nodes * kq / seq_s, "steps": kq,
                                "mode": "one context, cr_set_state / cr_step / cr_get_state (synchronous)"}},
         "roofline": roofline,
-        "clocks": dict(clocks, window="headline, fp64, batched and per-kernel timed regions") if clocks else None,
+        "clocks": dict(clocks, window="headline, fp64, batched, rkfr and per-kernel timed regions") if clocks else None,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()

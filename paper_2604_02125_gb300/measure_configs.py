@@ -7,7 +7,9 @@ Taylor-Green vortex, 512 batched 2D solves) and each form (FP64, FP32 pair
 fluxes) prints one JSON line: DOF-updates/s over K steps timed with CUDA
 events on the solver's stream (256 MiB L2 flush between steps), the mean
 volume and face/update kernel times, the FP32-vs-FP64 relative L2 after 100
-steps from the same state, and for the Taylor-Green vortex the FP64 kinetic
+steps from the same state, the same timings of the multi-stage RKFR scheme
+(one face exchange per RK stage) and its cost against the single-stage
+step, and for the Taylor-Green vortex the FP64 kinetic
 energy and entropy budgets over S steps; and the shear layer over its full
 run length (--long-steps, 2000): FP32 against FP64, conservation, budgets.
 
@@ -83,6 +85,20 @@ def measure_gpu(name, make, desc, steps, budget_steps):
             s.close()
         out["rel_l2_fp32_vs_fp64_after_100_steps"] = float(
             np.linalg.norm(finals["fp32"] - finals["fp64"]) / np.linalg.norm(finals["fp64"]))
+        # the multi-stage RKFR scheme on the same workload and kernels
+        out["rkfr"] = {}
+        for prec in ("fp64", "fp32"):
+            s = crkfr.Solver(mesh, prec=prec, stream=stream, scheme="rkfr")
+            s.set_state(U)
+            s.step(3)
+            s.sync()
+            ms = time_solver(s, steps, stream, flush)
+            vol, face = s.time_kernels(max(3, min(steps, 20)), flush)
+            out["rkfr"][prec] = {"dof_updates_per_s": nodes / (ms * 1e-3), "ms_per_step": ms,
+                                 "volume_ms_per_step": vol, "face_update_ms_per_step": face,
+                                 "crkfr_speedup": ms / out["forms"][prec]["ms_per_step"],
+                                 "status": crkfr.status_string(s.info()["status"])}
+            s.close()
         if name.startswith("tgv3d") and budget_steps > 0:
             out["budgets"] = {}
             for prec in ("fp64", "fp32"):

@@ -2,7 +2,9 @@
 
   python -m paper_2604_02125_gb300.run_case --case shear2d --cells 256 256 --N 3 --prec fp32 --steps 3
 
-Cases: wave1d, shear2d, mhd2d, tgv3d.  Prints the step count, time and dt.
+Cases: wave1d, shear2d, mhd2d, tgv3d; --scheme rkfr runs the multi-stage RKFR
+scheme instead of the single-stage cRKFR step.  Prints the step count, time
+and dt.
 """
 import argparse
 import os
@@ -29,18 +31,19 @@ def main(argv=None):
     ap.add_argument("--vol", default="ec")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--scheme", default="crkfr", choices=["crkfr", "rkfr"])
     a = ap.parse_args(argv)
     build.build()
     mesh, U = CASES[a.case](a.cells, a.N, a.vol)
-    with crkfr.Solver(mesh, prec=a.prec) as s:
+    with crkfr.Solver(mesh, prec=a.prec, scheme=a.scheme) as s:
         s.set_state(U)
         t0 = time.perf_counter()
         s.step(a.steps)
         s.sync()
         el = time.perf_counter() - t0
         info = s.info()
-    print("%s cells=%s N=%d %s: %d steps in %.3f s, t=%.6g dt=%.6g status=%d"
-          % (a.case, a.cells, a.N, a.prec, info["steps"], el, info["t"], info["dt"], info["status"]))
+    print("%s cells=%s N=%d %s %s: %d steps in %.3f s, t=%.6g dt=%.6g status=%d"
+          % (a.case, a.cells, a.N, a.prec, a.scheme, info["steps"], el, info["t"], info["dt"], info["status"]))
     return 0 if info["status"] == 0 else 1
 
 
