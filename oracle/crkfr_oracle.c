@@ -22,7 +22,8 @@
  *     (eqs. disc.avg.flux, local.time.avg.non.cons, Sec. 2.3),
  *   - time-averaged Rusanov flux (eq. numflux.cons) and the reduced-
  *     communication non-conservative numerical flux B(u^{n,+-}) g^avg(U)
- *     (Sec. 2.3, the variant used for all of the paper's results),
+ *     (Sec. 2.3, the variant used for all of the paper's results), or the
+ *     stage-wise one of eq. bad.numflux.non.cons (or_desc.ncflux = 1),
  *   - final update (eqs. crkfr.non.cons.final, total.F.non.cons) with the
  *     flux-differencing time-averaged volume term (Sec. 3);
  *   - the multi-stage RKFR step the cRKFR method is derived from (eq.
@@ -63,6 +64,11 @@ typedef struct {
   double gamma, cfl, c_h;
   int vol;         /* 0 = EC (Ranocha / GLM-MHD EC), 1 = KEP Kennedy-Gruber, 2 = central */
   int surf;        /* 0 = Rusanov, 1 = EC two-point surface flux (semi-discrete tests) */
+  int ncflux;      /* non-conservative numerical flux of the cRKFR step (Sec. 2.3):
+                      0 = B(u^{n,+-}) g^avg(U) (reduced communication, all of the paper's results),
+                      1 = sum_j b_j B(u^{(j),+-}) g^avg(u^(j)) (eq. bad.numflux.non.cons)      */
+  int tab_s;       /* > 0: use this explicit RK tableau instead of the degree's (tests)   */
+  const double *tab_A, *tab_b;   /* [7][7] row-major, [7]                            */
 } or_desc;
 
 /* ------------------------------------------------------------------------- */
@@ -420,6 +426,12 @@ static int mesh_setup(const or_desc *d, or_mesh *m) {
   }
   double A[OR_MAXS * OR_MAXS], b[OR_MAXS];
   if (or_butcher(d->N, &m->S, A, b)) return -1;
+  if (d->tab_s > 0) {
+    if (d->tab_s > OR_MAXS || !d->tab_A || !d->tab_b) return -1;
+    m->S = d->tab_s;
+    for (int k = 0; k < OR_MAXS * OR_MAXS; ++k) A[k] = d->tab_A[k];
+    for (int k = 0; k < OR_MAXS; ++k) b[k] = d->tab_b[k];
+  }
   for (int i = 0; i < OR_MAXS; ++i) { m->b[i] = b[i]; for (int j = 0; j < OR_MAXS; ++j) m->A[i][j] = A[i * OR_MAXS + j]; }
   return 0;
 }
@@ -529,13 +541,15 @@ typedef struct {
   double *Fbar;      /* [dim][E][np][M]      sum_i b_i f^dir(u^(i))             */
   double *Fnc;       /* [dim][E][np][M]      sum_i b_i B^dir(u^(i)) g^dir(u^(i)) */
   double *un;        /* [E][np][M]           u^n per element                    */
+  double *Us;        /* [E][S][np][M]        stage states u^(i) (ncflux 1 only) */
 } or_work;
 
 /* The cRK inner stages of one element (eq. crkfr.inner) and its time averages
  * (eqs. disc.avg.flux, local.time.avg.non.cons and the flux-differencing final
  * volume term of Sec. 3). */
 static void element_stages(const or_desc *d, const or_mesh *m, const double *une, double dt,
-                           double *Rbar, double *Ubar, double *Fbar /*[dim][np][M] stride np*M*/, double *Fnc) {
+                           double *Rbar, double *Ubar, double *Fbar /*[dim][np][M] stride np*M*/, double *Fnc,
+                           double *Ust /* [S][np][M] stage states, or NULL */) {
   int M = m->M, np = m->np, S = m->S;
   size_t sz = (size_t)np * M;
   double *us = malloc(sizeof(double) * sz * S);
@@ -551,6 +565,8 @@ static void element_stages(const or_desc *d, const or_mesh *m, const double *une
       us[i * sz + k] = une[k] - dt * acc;
     }
     local_residual(d, m, &us[i * sz], &R[i * sz]);
+    if (Ust)
+      for (size_t k = 0; k < sz; ++k) Ust[i * sz + k] = us[i * sz + k];
     double bi = m->b[i];
     for (size_t k = 0; k < sz; ++k) { Rbar[k] += bi * R[i * sz + k]; Ubar[k] += bi * us[i * sz + k]; }
     for (int p = 0; p < np; ++p)
@@ -586,7 +602,7 @@ typedef struct {
   int nloc;
 } or_set;
 
-static void set_alloc(or_set *S, int E, int nloc, size_t sz, int dim) {
+static void set_alloc(or_set *S, int E, int nloc, size_t sz, int dim, int stages) {
   S->nloc = nloc;
   S->loc = malloc(sizeof(int) * E);
   for (int e = 0; e < E; ++e) S->loc[e] = -1;
@@ -595,9 +611,10 @@ static void set_alloc(or_set *S, int E, int nloc, size_t sz, int dim) {
   S->W.Fbar = malloc(sizeof(double) * sz * nloc * dim);
   S->W.Fnc = malloc(sizeof(double) * sz * nloc * dim);
   S->W.un = malloc(sizeof(double) * sz * nloc);
+  S->W.Us = stages > 0 ? malloc(sizeof(double) * sz * nloc * stages) : NULL;
 }
 static void set_free(or_set *S) {
-  free(S->loc); free(S->W.Rbar); free(S->W.Ubar); free(S->W.Fbar); free(S->W.Fnc); free(S->W.un);
+  free(S->loc); free(S->W.Rbar); free(S->W.Ubar); free(S->W.Fbar); free(S->W.Fnc); free(S->W.un); free(S->W.Us);
 }
 
 /* 1. element-local stages and time averages of element e into local slot k */
@@ -607,7 +624,8 @@ static void set_stages(const or_desc *d, const or_mesh *m, const double *Un, dou
   double *fb = malloc(sizeof(double) * sz * dim), *fn = malloc(sizeof(double) * sz * dim);
   S->loc[e] = k;
   gather_elem(m, Un, e, &S->W.un[k * sz]);
-  element_stages(d, m, &S->W.un[k * sz], dt, &S->W.Rbar[k * sz], &S->W.Ubar[k * sz], fb, fn);
+  element_stages(d, m, &S->W.un[k * sz], dt, &S->W.Rbar[k * sz], &S->W.Ubar[k * sz], fb, fn,
+                 S->W.Us ? &S->W.Us[(size_t)k * m->S * sz] : NULL);
   for (int dir = 0; dir < dim; ++dir)
     for (size_t q = 0; q < sz; ++q) {
       S->W.Fbar[((size_t)dir * S->nloc + k) * sz + q] = fb[dir * sz + q];
@@ -656,13 +674,26 @@ static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int 
         double lam = lm > lp ? lm : lp;
         double Fnum[OR_MAXM], ncs[OR_MAXM];
         for (int v = 0; v < M; ++v) Fnum[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * lam * (Up[v] - Um[v]);
-        /* F^{num,+-}_nc = B(u^{n,+-}) g^avg(U); the jump F^num_{+-} - F^tot_{+-} */
+        /* F^{num,+-}_nc = B(u^{n,+-}) g^avg(U), or with ncflux 1 (eq. bad.numflux.non.cons)
+         * sum_j b_j B(u^{(j),+-}) g^avg(u^(j)) from the stage traces of both sides;
+         * then the jump F^num_{+-} - F^tot_{+-} */
         double J[OR_MAXM];
+        if (d->ncflux == 1) {
+          for (int v = 0; v < M; ++v) ncs[v] = 0.0;
+          for (int j = 0; j < m->S; ++j) {
+            const double *sel = &W->Us[((size_t)ke * m->S + j) * sz], *snb = &W->Us[((size_t)kn * m->S + j) * sz];
+            double sm[OR_MAXM], sp[OR_MAXM], nj[OR_MAXM];
+            if (side) { extrapolate(d, m, sel, dir, 1, fijk, sm); extrapolate(d, m, snb, dir, 0, fijk, sp); }
+            else      { extrapolate(d, m, snb, dir, 1, fijk, sm); extrapolate(d, m, sel, dir, 0, fijk, sp); }
+            nc_with_gavg(d, dir, side ? sm : sp, sm, sp, nj);
+            for (int v = 0; v < M; ++v) ncs[v] += m->b[j] * nj[v];
+          }
+        } else {
+          nc_with_gavg(d, dir, side ? um : up, Um, Up, ncs);
+        }
         if (side) {
-          nc_with_gavg(d, dir, um, Um, Up, ncs);
           for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fm[v] + Nm[v]);
         } else {
-          nc_with_gavg(d, dir, up, Um, Up, ncs);
           for (int v = 0; v < M; ++v) J[v] = Fnum[v] + ncs[v] - (Fp[v] + Np_[v]);
         }
         /* - dt J d_x g_R (side 1) or - dt J d_x g_L (side 0), at every node of the line */
@@ -685,7 +716,7 @@ int or_step(const or_desc *d, const double *Un, double dt, double *Unew) {
   int M = m.M, np = m.np, E = m.E;
   size_t sz = (size_t)np * M;
   or_set S;
-  set_alloc(&S, E, E, sz, d->dim);
+  set_alloc(&S, E, E, sz, d->dim, d->ncflux == 1 ? m.S : 0);
   for (int e = 0; e < E; ++e) set_stages(d, &m, Un, dt, &S, e, e);
   for (int e = 0; e < E; ++e) {
     double unew[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
@@ -709,7 +740,7 @@ int or_step_elements(const or_desc *d, const double *Un, double dt, int nsel, co
   for (int k = 0; k < nsel; ++k)
     if (sel[k] < 0 || sel[k] >= E) return -1;
   or_set S;
-  set_alloc(&S, E, nsel * (1 + 2 * dim), sz, dim);
+  set_alloc(&S, E, nsel * (1 + 2 * dim), sz, dim, d->ncflux == 1 ? m.S : 0);
   int nloc = 0;
   for (int k = 0; k < nsel; ++k) {
     int need[7];
@@ -737,7 +768,7 @@ int or_step_elements(const or_desc *d, const double *Un, double dt, int nsel, co
 int or_element_stages(const or_desc *d, const double *une, double dt, double *Rbar, double *Ubar, double *Fbar, double *Fnc) {
   or_mesh m;
   if (mesh_setup(d, &m)) return -1;
-  element_stages(d, &m, une, dt, Rbar, Ubar, Fbar, Fnc);
+  element_stages(d, &m, une, dt, Rbar, Ubar, Fbar, Fnc, NULL);
   return 0;
 }
 

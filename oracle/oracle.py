@@ -18,6 +18,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 EQ = {"euler": 0, "glm_mhd": 1}
 VOL = {"ec": 0, "kep": 1, "central": 2}
 SURF = {"rusanov": 0, "ec": 1}
+NCFLUX = {"reduced": 0, "stages": 1}
 
 
 def build(force=False):
@@ -39,7 +40,9 @@ class Desc(ctypes.Structure):
                 ("cells", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
-                ("vol", ctypes.c_int), ("surf", ctypes.c_int)]
+                ("vol", ctypes.c_int), ("surf", ctypes.c_int), ("ncflux", ctypes.c_int),
+                ("tab_s", ctypes.c_int), ("tab_A", ctypes.POINTER(ctypes.c_double)),
+                ("tab_b", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -83,7 +86,9 @@ def _ptr(a):
 def make_desc(mesh):
     """Build the oracle descriptor from a mesh dict (keys as in
     paper_2604_02125_gb300.inputs: eq, dim, N, cells, lo, hi, gamma, cfl,
-    c_h, vol, surf)."""
+    c_h, vol, surf; optional: ncflux 'reduced' | 'stages' (the non-conservative
+    numerical flux of the cRKFR step), tableau (A, b): an explicit RK tableau
+    of s <= 7 stages in place of the degree's)."""
     d = Desc()
     d.eq = EQ[mesh.get("eq", "euler")]
     d.dim = mesh["dim"]
@@ -100,6 +105,18 @@ def make_desc(mesh):
     d.c_h = mesh.get("c_h", 0.0)
     d.vol = VOL[mesh.get("vol", "ec")]
     d.surf = SURF[mesh.get("surf", "rusanov")]
+    d.ncflux = NCFLUX[mesh.get("ncflux", "reduced")]
+    if mesh.get("tableau") is not None:
+        A, b = mesh["tableau"]
+        s = len(b)
+        A7 = np.zeros((7, 7))
+        A7[:s, :s] = np.asarray(A, dtype=np.float64)[:s, :s]
+        b7 = np.zeros(7)
+        b7[:s] = b
+        d._keep = (A7, b7)            # the descriptor points into these arrays
+        d.tab_s = s
+        d.tab_A = _ptr(A7)
+        d.tab_b = _ptr(b7)
     return d
 
 
