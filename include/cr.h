@@ -64,6 +64,13 @@ extern "C" {
                                   face exchange (Rusanov flux of the stage traces) at every
                                   stage; for measuring the single-stage advantage                */
 
+/* non-conservative numerical flux of the cRKFR step (GLM-MHD) */
+#define CR_NCFLUX_REDUCED 0    /* B(u^{n,+-}) g^avg(U) from the time-averaged records: no data beyond
+                                  the conservative flux's (Sec. 2.3; all of the paper's results)  */
+#define CR_NCFLUX_STAGES  1    /* sum_j b_j B(u^{(j),+-}) g^avg(u^(j)) (eq. bad.numflux.non.cons):
+                                  the face traces of every stage are exchanged (seven values per
+                                  stage and face node); GLM-MHD with CR_SCHEME_CRKFR only        */
+
 /* arithmetic of the element-local work */
 #define CR_FP64          0     /* every step of the path in FP64                        */
 #define CR_FP32_PAIRFLUX 1     /* stages, pair fluxes, time averages and face fluxes in
@@ -85,6 +92,8 @@ typedef struct {
   int prec;          /* CR_FP64 | CR_FP32_PAIRFLUX                                      */
   int scheme;        /* CR_SCHEME_CRKFR (0) | CR_SCHEME_RKFR; the batched form and
                         cr_step_noalloc take CR_SCHEME_CRKFR only                        */
+  int ncflux;        /* CR_NCFLUX_REDUCED (0) | CR_NCFLUX_STAGES; the batched form and
+                        cr_step_noalloc take CR_NCFLUX_REDUCED only                      */
 } cr_mesh_desc;
 
 typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
@@ -105,7 +114,7 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
  * The library allocates and owns all device buffers (state, stage/trace
  * scratch, step records; CR_SCHEME_RKFR adds a stage state and s - 1 stage
- * increments).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+ * increments, CR_NCFLUX_STAGES the stage traces after the face records).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
 /* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */
@@ -196,7 +205,7 @@ int cr_check_conversions(long long n, unsigned long long seed, long long *mismat
  *   dt_out     : device pointer receiving the dt used (FP64), or NULL.
  *   cuda_stream: stream for all work (asynchronous; nothing is synchronised).
  * dt follows the descriptor (CFL rule on u^n, or dt_fixed); desc->scheme must
- * be CR_SCHEME_CRKFR (CR_EINVAL otherwise).  The scratch
+ * be CR_SCHEME_CRKFR and desc->ncflux CR_NCFLUX_REDUCED (CR_EINVAL otherwise).  The scratch
  * (residual sums, face traces, reductions, step record) lives in one static
  * device array of CR_NOALLOC_SCRATCH_BYTES per device, held until the
  * process exits; a mesh needing more returns CR_ETOOLARGE (roughly 80k nodes

@@ -20,6 +20,7 @@ VOL = {"ec": 0, "kep": 1, "central": 2}
 SURF = {"rusanov": 0}
 PREC = {"fp64": 0, "fp32": 1}
 SCHEME = {"crkfr": 0, "rkfr": 1}
+NCFLUX = {"reduced": 0, "stages": 1}
 
 
 class CrError(RuntimeError):
@@ -33,7 +34,7 @@ class MeshDesc(ctypes.Structure):
                 ("cells", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("vol", ctypes.c_int), ("surf", ctypes.c_int),
-                ("prec", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("scheme", ctypes.c_int), ("ncflux", ctypes.c_int)]
 
 
 _lib = None
@@ -87,7 +88,9 @@ def status_string(s):
 
 def make_desc(mesh, prec="fp64", dt_fixed=0.0, scheme=None):
     """Descriptor of a mesh dict; scheme ('crkfr' or 'rkfr', the multi-stage
-    scheme) defaults to the dict's 'scheme' key, else 'crkfr'."""
+    scheme) defaults to the dict's 'scheme' key, else 'crkfr'; the dict's
+    'ncflux' key ('reduced' or 'stages', GLM-MHD) selects the non-conservative
+    numerical flux."""
     d = MeshDesc()
     d.eq = EQ[mesh.get("eq", "euler")]
     d.dim = mesh["dim"]
@@ -105,6 +108,7 @@ def make_desc(mesh, prec="fp64", dt_fixed=0.0, scheme=None):
     d.surf = SURF[mesh.get("surf", "rusanov")]
     d.prec = PREC[prec]
     d.scheme = SCHEME[scheme or mesh.get("scheme", "crkfr")]
+    d.ncflux = NCFLUX[mesh.get("ncflux", "reduced")]
     return d
 
 

@@ -83,7 +83,13 @@ void ref_tables(int N, double* xi, double* w, double D[6][6]) {
   }
 }
 
-bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o) {
+bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o, int ncflux) {
+  if (ncflux == CR_NCFLUX_STAGES) {
+    if (eq != CR_GLM_MHD || dim != 2) return false;
+    if (prec == CR_FP64) return vol == 0 ? ops_mhd2s_fp64_ec(N, o) : vol == 2 ? ops_mhd2s_fp64_central(N, o) : false;
+    return vol == 0 ? ops_mhd2s_fp32_ec(N, o) : vol == 2 ? ops_mhd2s_fp32_central(N, o) : false;
+  }
+  if (ncflux != CR_NCFLUX_REDUCED) return false;
   struct Entry {
     int eq, dim, prec, vol;
     bool (*fn)(int, VariantOps*);
@@ -244,6 +250,10 @@ static bool desc_valid(const cr_mesh_desc& d) {
   if (d.vol < 0 || d.vol > 2 || d.surf != CR_SURF_RUSANOV) return false;
   if (d.prec != CR_FP64 && d.prec != CR_FP32_PAIRFLUX) return false;
   if (d.scheme != CR_SCHEME_CRKFR && d.scheme != CR_SCHEME_RKFR) return false;
+  // the stage-wise non-conservative flux: GLM-MHD, single-stage scheme
+  if (d.ncflux != CR_NCFLUX_REDUCED &&
+      (d.ncflux != CR_NCFLUX_STAGES || d.eq != CR_GLM_MHD || d.scheme != CR_SCHEME_CRKFR))
+    return false;
   if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || d.dt_fixed < 0.0 || !(d.c_h >= 0.0)) return false;
   for (int k = 0; k < d.dim; ++k) {
     if (d.cells[k] < 1) return false;
@@ -302,7 +312,7 @@ static int capture(cr_ctx* c, int steps, int parity, cudaGraphExec_t* out) {
 
 static int init_single(cr_ctx* c) {
   const cr_mesh_desc& d = c->desc[0];
-  if (!get_ops(d.eq, d.dim, d.prec, d.vol, d.degree_N, &c->ops)) return CR_EINVAL;
+  if (!get_ops(d.eq, d.dim, d.prec, d.vol, d.degree_N, &c->ops, d.ncflux)) return CR_EINVAL;
   const VariantOps& o = c->ops;
   c->M = o.M;
   c->NP = o.NP;
@@ -323,7 +333,7 @@ static int init_single(cr_ctx* c) {
   };
   al((void**)&lc.u, sizeof(double) * (size_t)o.M * nodes);
   al(&lc.rbar, o.real_bytes * (size_t)o.M * nodes);
-  al(&lc.trace, o.real_bytes * (size_t)o.dim * 2 * o.C * NFt);
+  al(&lc.trace, o.real_bytes * ((size_t)o.dim * 2 * o.C * NFt + o.ncs_per_elem * (size_t)E));
   al((void**)&lc.st, sizeof(DevState));
   al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
   if (d.scheme == CR_SCHEME_RKFR) {

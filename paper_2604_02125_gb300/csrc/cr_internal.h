@@ -44,6 +44,7 @@ struct BatchLaunch {
 
 struct VariantOps {
   int M, NP, NF, C, dim;       // C: components of a face record
+  size_t ncs_per_elem;         // stage-wise non-conservative flux: stage-trace values per element after the records
   size_t vol_bytes_per_elem;   // shared memory per element of the tile volume kernel
   bool lanes;                  // the lane-form volume kernel is used (32 elements per CTA)
   size_t (*vol_smem)(int epb); // dynamic shared memory of one volume CTA
@@ -89,6 +90,10 @@ bool ops_mhd2_fp64_ec(int N, VariantOps* o);
 bool ops_mhd2_fp64_central(int N, VariantOps* o);
 bool ops_mhd2_fp32_ec(int N, VariantOps* o);
 bool ops_mhd2_fp32_central(int N, VariantOps* o);
+bool ops_mhd2s_fp64_ec(int N, VariantOps* o);
+bool ops_mhd2s_fp64_central(int N, VariantOps* o);
+bool ops_mhd2s_fp32_ec(int N, VariantOps* o);
+bool ops_mhd2s_fp32_central(int N, VariantOps* o);
 
 // reference-element tables on [0,1] computed on the host (Newton on P_N', barycentric D)
 void ref_tables(int N, double* xi, double* w, double D[6][6]);
@@ -96,8 +101,10 @@ void ref_tables(int N, double* xi, double* w, double D[6][6]);
 // reference-element and tableau tables of degree N in both precisions
 void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32);
 
-// launchers of a (system, dim, precision, degree) variant; false if none
-bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o);
+// launchers of a (system, dim, precision, degree) variant; false if none;
+// ncflux = CR_NCFLUX_STAGES selects the GLM-MHD kernels with the stage-wise
+// non-conservative flux
+bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o, int ncflux = 0);
 
 // elements per CTA of the volume kernel used by every context of a variant
 int default_epb(const VariantOps& o);

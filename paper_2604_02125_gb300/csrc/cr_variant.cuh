@@ -210,6 +210,7 @@ struct Variant {
     o->NP = L::NP;
     o->NF = L::NF;
     o->C = trace_comps<EQ>();
+    o->ncs_per_elem = EQ::NCS ? ncs_values_per_elem<EQ, N>() : 0;
     o->dim = EQ::DIM;
     o->vol_bytes_per_elem = L::bytes_per_elem();
     o->lanes = kLanes;

@@ -167,6 +167,29 @@ template <class EQ, int NF>
 __host__ __device__ __forceinline__ size_t trace_index(int d, int side, int f, int c, long long E, long long e) {
   return ((((size_t)(d * 2 + side) * NF + f) * trace_comps<EQ>() + c) * (size_t)E) + (size_t)e;
 }
+// Stage-wise non-conservative flux (EQ::NCS): after the records, the seven
+// primitives of every stage's face trace, [DIM][2][NF][stage][7][E].
+template <class EQ, int N>
+__host__ __device__ constexpr size_t ncs_values_per_elem() {
+  return (size_t)EQ::DIM * 2 * (ipow(N + 1, EQ::DIM) / (N + 1)) * rk_stages(N) * 7;
+}
+template <class EQ, int N>
+__host__ __device__ __forceinline__ size_t ncs_index(int d, int side, int f, int j, int c, long long E, long long e) {
+  constexpr int NF = ipow(N + 1, EQ::DIM) / (N + 1), S = rk_stages(N);
+  const size_t base = (size_t)EQ::DIM * 2 * NF * trace_comps<EQ>() * (size_t)E;
+  return base + (((((size_t)(d * 2 + side) * NF + f) * S + j) * 7 + c) * (size_t)E) + (size_t)e;
+}
+// the primitives of stage j at face node f of face (d, side) of element e
+template <class EQ, int N, typename R>
+__device__ __forceinline__ void write_stage_prims(R* __restrict__ trace, int d, int side, int f, int j, long long E,
+                                                  long long e, const R* q) {
+  if constexpr (EQ::NCS) {
+    R w[7];
+    EQ::stage_prims(q, w);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) trace[ncs_index<EQ, N>(d, side, f, j, c, E, e)] = w[c];
+  }
+}
 
 template <class EQ, int N, typename R>
 struct VolLayout {
@@ -269,6 +292,19 @@ __device__ __forceinline__ void volume_tile_body(const double* __restrict__ u, R
         EQ::pair_data(uu, q, pp);
 #pragma unroll
         for (int c = 0; c < P; ++c) my[L::O_Q + c * NP + p] = q[c];
+        if constexpr (EQ::NCS) {
+          // face traces of this stage (stage-wise non-conservative flux)
+          int rq = p;
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            const int cq = rq % n;
+            rq /= n;
+            const int stride = ipow(n, d);
+            if (cq == 0 || cq == N)
+              write_stage_prims<EQ, N, R>(trace, d, cq == N ? 1 : 0, (p % stride) + (p / (stride * n)) * stride, i, E,
+                                          e0 + el, q);
+          }
+        }
 #pragma unroll
         for (int v = 0; v < M; ++v) my[L::O_RS + (i * M + v) * NP + p] = R(0);
         // which faces this node lies on
@@ -474,15 +510,18 @@ __device__ __forceinline__ void jump_of(const R* o, const R* x, int d, int side_
 #pragma unroll
   for (int v = 0; v < M; ++v) J[v] = R(0.5) * (o[M + v] + x[M + v]) - R(0.5) * lam * sgn * (x[v] - o[v]) - o[M + v];
   if constexpr (EQ::NC) {
-    // + B(u^n_own) g^avg(U) - F^nc_own
-    R un[M], q[EQ::P];
+    // + B(u^n_own) g^avg(U) - F^nc_own (the stage-wise flux adds its own sum
+    // in face_jump instead of the first term)
+    if constexpr (!EQ::NCS) {
+      R un[M], q[EQ::P];
 #pragma unroll
-    for (int v = 0; v < M; ++v) un[v] = o[3 * M + 1 + v];
-    EQ::pair_data(un, q, pp);
-    R g[2];
-    g[0] = R(0.5) * (o[5 + d] + x[5 + d]);
-    g[1] = R(0.5) * (o[8] + x[8]);
-    EQ::nc_apply(d, q, g, J);
+      for (int v = 0; v < M; ++v) un[v] = o[3 * M + 1 + v];
+      EQ::pair_data(un, q, pp);
+      R g[2];
+      g[0] = R(0.5) * (o[5 + d] + x[5 + d]);
+      g[1] = R(0.5) * (o[8] + x[8]);
+      EQ::nc_apply(d, q, g, J);
+    }
 #pragma unroll
     for (int v = 0; v < M; ++v) J[v] -= o[2 * M + 1 + v];
   }
@@ -490,12 +529,34 @@ __device__ __forceinline__ void jump_of(const R* o, const R* x, int d, int side_
 
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
-                                          long long e_oth, int f, R* J, const PhysParams<R>& pp) {
+                                          long long e_oth, int f, R* J, const PhysParams<R>& pp, const RefTab<R>& tb) {
   constexpr int C = trace_comps<EQ>();
   R o[C], x[C];
   load_face_record<EQ, N, R>(trace, E, d, side_own, f, e_own, o);
   load_face_record<EQ, N, R>(trace, E, d, 1 - side_own, f, e_oth, x);
   jump_of<EQ, R>(o, x, d, side_own, J, pp);
+  if constexpr (EQ::NCS) {
+    // + sum_j b_j B(u^(j)_own) g^avg(u^(j)) (eq. bad.numflux.non.cons)
+#pragma unroll 1
+    for (int j = 0; j < rk_stages(N); ++j) {
+      R wo[7], wx[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        wo[c] = trace[ncs_index<EQ, N>(d, side_own, f, j, c, E, e_own)];
+        wx[c] = trace[ncs_index<EQ, N>(d, 1 - side_own, f, j, c, E, e_oth)];
+      }
+      R go[2], gx[2], g[2], nc[EQ::M];
+      EQ::ncg_prims(d, wo, go);
+      EQ::ncg_prims(d, wx, gx);
+      g[0] = R(0.5) * (go[0] + gx[0]);
+      g[1] = R(0.5) * (go[1] + gx[1]);
+#pragma unroll
+      for (int v = 0; v < EQ::M; ++v) nc[v] = R(0);
+      EQ::nc_apply_prims(d, wo, g, nc);
+#pragma unroll
+      for (int v = 0; v < EQ::M; ++v) J[v] += tb.b[j] * nc[v];
+    }
+  }
 }
 
 // RK = true: stage mode of the multi-stage RKFR step (RkStage)
@@ -531,7 +592,7 @@ __device__ __forceinline__ void face_update_body(double* __restrict__ u, const R
       if (cd == N) {   // face xi_d = 1: element is the '-' state
         const unsigned nb = neighbour_of(e, ec, d, +1, ma);
         R J[M];
-        face_jump<EQ, N, R>(trace, E, d, 1, e, nb, f, J, pp);
+        face_jump<EQ, N, R>(trace, E, d, 1, e, nb, f, J, pp, tb);
         const R s = dtR * tb.iwN * inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int v = 0; v < M; ++v) du[v] -= s * J[v];
@@ -539,7 +600,7 @@ __device__ __forceinline__ void face_update_body(double* __restrict__ u, const R
       if (cd == 0) {   // face xi_d = 0: element is the '+' state
         const unsigned nb = neighbour_of(e, ec, d, -1, ma);
         R J[M];
-        face_jump<EQ, N, R>(trace, E, d, 0, e, nb, f, J, pp);
+        face_jump<EQ, N, R>(trace, E, d, 0, e, nb, f, J, pp, tb);
         const R s = dtR * tb.iw0 * inv_dx_of<R>(ma, d);
 #pragma unroll
         for (int v = 0; v < M; ++v) du[v] += s * J[v];

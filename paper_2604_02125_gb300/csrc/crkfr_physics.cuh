@@ -209,6 +209,7 @@ struct Euler {
   static constexpr int M = DIM_ + 2;
   static constexpr int P = DIM_ + 3;
   static constexpr bool NC = false;
+  static constexpr bool NCS = false;   // stage-wise non-conservative flux (GLM-MHD only)
   static constexpr int IRHO = 0, IP = DIM_ + 1, IAUX = DIM_ + 2;
 
   template <typename R>
@@ -359,6 +360,7 @@ struct GlmMhd {
   static constexpr int M = 9;
   static constexpr int P = 13;
   static constexpr bool NC = true;
+  static constexpr bool NCS = false;
   static constexpr int IRHO = 0, IP = 4, IB = 5, IPSI = 8, IBETA = 9, IV2 = 10, IB2 = 11, IVB = 12;
 
   template <typename R>
@@ -502,6 +504,39 @@ struct GlmMhd {
     }
     lam_sum = tot;
     return rho > T(0) && p > T(0) && isfinite(tot);
+  }
+};
+
+// GLM-MHD with the stage-wise non-conservative numerical flux of eq.
+// bad.numflux.non.cons: sum_j b_j B(u^{(j),+-}) g^avg(u^(j)).  B(u) and g(u)
+// depend on u through v, B and psi only, so each stage leaves these seven
+// values of both face traces for the face kernel (stage_prims), which applies
+// B(own) to the averaged g of both sides (nc_apply_prims).
+template <int VOL_ = VOL_EC>
+struct GlmMhdStages : GlmMhd<VOL_> {
+  using Base = GlmMhd<VOL_>;
+  static constexpr bool NCS = true;
+  static constexpr int NPRIM = 7;   // v1, v2, v3, B1, B2, B3, psi
+  template <typename R>
+  __device__ __forceinline__ static void stage_prims(const R* q, R* o) {
+    o[0] = q[1]; o[1] = q[2]; o[2] = q[3];
+    o[3] = q[Base::IB]; o[4] = q[Base::IB + 1]; o[5] = q[Base::IB + 2]; o[6] = q[Base::IPSI];
+  }
+  // g^d of a primitive record: (B_d, psi)
+  template <typename R>
+  __device__ __forceinline__ static void ncg_prims(int d, const R* w, R* g) { g[0] = w[3 + d]; g[1] = w[6]; }
+  // out += phi_Powell(w) g0 + phi_GLM^d(w) g1 (as nc_apply, from the primitives)
+  template <typename R>
+  __device__ __forceinline__ static void nc_apply_prims(int d, const R* w, const R* g, R* out) {
+    const R g0 = g[0], g1 = g[1];
+    out[1] += w[3] * g0;
+    out[2] += w[4] * g0;
+    out[3] += w[5] * g0;
+    out[4] += (w[0] * w[3] + w[1] * w[4] + w[2] * w[5]) * g0 + w[d] * w[6] * g1;
+    out[5] += w[0] * g0;
+    out[6] += w[1] * g0;
+    out[7] += w[2] * g0;
+    out[8] += w[d] * g1;
   }
 };
 

@@ -382,6 +382,12 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
           for (int c = 0; c < P; ++c) my[L::O_Q + c * NP + p] = q[k][c];
         }
       }
+      if constexpr (EQ::NCS) {
+        // face traces of this stage at the ends of the x-line (stage-wise
+        // non-conservative flux)
+        write_stage_prims<EQ, N, R>(trace, 0, 0, l, i, E, e0 + el, q[0]);
+        write_stage_prims<EQ, N, R>(trace, 0, 1, l, i, E, e0 + el, q[N]);
+      }
       // ---------------- x-direction flux differencing, all in registers
       // (packed form: together with the y-line below)
       if constexpr (!PACK) {
@@ -434,6 +440,11 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < P; ++c) qy[k][c] = my[L::O_Q + c * NP + base + k * n];
+        if constexpr (EQ::NCS) {
+          static_assert(DIM == 2, "stage-wise non-conservative flux: 2D only");
+          write_stage_prims<EQ, N, R>(trace, 1, 0, l, i, E, e0 + el, qy[0]);
+          write_stage_prims<EQ, N, R>(trace, 1, 1, l, i, E, e0 + el, qy[N]);
+        }
         line_residual<EQ, N, R, (DIM > 1 ? 1 : 0)>(qy, ay, fend, pp, tb, inv_dx_of<R>(ma, 1));
         face_accumulate<EQ, N, R, (DIM > 1 ? 1 : 0)>(fy, qy, fend, bi, i == 0, pp);
 #pragma unroll
@@ -682,14 +693,14 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
     }
     elem_coords<DIM>(e, ma, ec);
     // ---- phase A: x faces at the own line's ends, face node l of the y / z faces
-    face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp);
-    face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp);
+    face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp, tb);
+    face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp, tb);
 #pragma unroll
     for (int d = 1; d < DIM; ++d)
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         R J[M];
-        face_jump<EQ, N, R>(trace, E, d, side, e, neighbour_of(e, ec, d, side ? +1 : -1, ma), l, J, pp);
+        face_jump<EQ, N, R>(trace, E, d, side, e, neighbour_of(e, ec, d, side ? +1 : -1, ma), l, J, pp, tb);
         const R sc = side ? -(dtR * tb.iwN * inv_dx_of<R>(ma, d)) : dtR * tb.iw0 * inv_dx_of<R>(ma, d);
         R* dst = sj + ((size_t)(((d - 1) * 2 + side) * NF + l) * M) * 32 + el;
 #pragma unroll

@@ -1,0 +1,6 @@
+// Instantiation of the cRKFR kernels for one (system, precision, volume flux); N = 1..5.
+// GLM-MHD with the stage-wise non-conservative numerical flux (eq. bad.numflux.non.cons).
+#include "cr_variant.cuh"
+namespace crk {
+bool ops_mhd2s_fp64_central(int N, VariantOps* o) { return fill_ops<GlmMhdStages<VOL_CENTRAL>, double>(N, o); }
+}  // namespace crk

@@ -55,15 +55,17 @@ def test_descriptor_layout_matches_c(tmp_path):
     from paper_2604_02125_gb300 import crkfr
     src = tmp_path / "lay.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cr.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cr_mesh_desc),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cr_mesh_desc),'
                    'offsetof(cr_mesh_desc, lo), offsetof(cr_mesh_desc, gamma),'
-                   'offsetof(cr_mesh_desc, dt_fixed), offsetof(cr_mesh_desc, prec), offsetof(cr_mesh_desc, scheme));'
+                   'offsetof(cr_mesh_desc, dt_fixed), offsetof(cr_mesh_desc, prec), offsetof(cr_mesh_desc, scheme),'
+                   'offsetof(cr_mesh_desc, ncflux));'
                    ' return 0;}\n')
     exe = tmp_path / "lay"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     D = crkfr.MeshDesc
-    assert got == [ctypes.sizeof(D), D.lo.offset, D.gamma.offset, D.dt_fixed.offset, D.prec.offset, D.scheme.offset]
+    assert got == [ctypes.sizeof(D), D.lo.offset, D.gamma.offset, D.dt_fixed.offset, D.prec.offset, D.scheme.offset,
+                   D.ncflux.offset]
 
 
 def _init_status(lib, mesh, prec="fp64"):
@@ -86,10 +88,15 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
         assert _init_status(lib, m) == crkfr.CR_EINVAL, m
     d = crkfr.make_desc(base)
     h = ctypes.c_void_p()
-    for field, value in (("surf", 1), ("prec", 2), ("vol", 3), ("dt_fixed", -1.0), ("scheme", 2), ("scheme", -1)):
+    for field, value in (("surf", 1), ("prec", 2), ("vol", 3), ("dt_fixed", -1.0), ("scheme", 2), ("scheme", -1),
+                         ("ncflux", 2), ("ncflux", 1)):           # the stage-wise flux is for GLM-MHD only
         d2 = crkfr.make_desc(base)
         setattr(d2, field, value)
         assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL, field
+    # ... and for the single-stage scheme only
+    mh = inputs.mesh_dict("glm_mhd", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 5.0 / 3.0, c_h=1.0)
+    d2 = crkfr.make_desc(dict(mh, ncflux="stages"), scheme="rkfr")
+    assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL
     assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d), 0, None) == crkfr.CR_EINVAL
 
 
@@ -107,4 +114,7 @@ def test_noalloc_size_limit_without_gpu(lib):
     # the allocation-free step is the single-stage scheme only
     rk = crkfr.make_desc(inputs.mesh_dict("euler", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 1.4), scheme="rkfr")
     assert lib.cr_step_noalloc(ctypes.byref(rk), dummy, dummy, None, None) == crkfr.CR_EINVAL
+    ns = crkfr.make_desc(dict(inputs.mesh_dict("glm_mhd", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 5.0 / 3.0, c_h=1.0),
+                              ncflux="stages"))
+    assert lib.cr_step_noalloc(ctypes.byref(ns), dummy, dummy, None, None) == crkfr.CR_EINVAL
     assert lib.cr_step_noalloc(None, dummy, dummy, None, None) == crkfr.CR_EINVAL
