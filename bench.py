@@ -451,6 +451,25 @@ def main():
                 "peak": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm else None,
                 "frac": (fbytes / (face_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                 "bytes_per_launch": fbytes, "traffic": fprof[1] if fprof else None}
+    # multi-stage RKFR, FP32 form: the face/update stages against HBM, the
+    # single-stage volume launches against the FP32 peak (same flops as the
+    # cRKFR volume kernel: every stage's flux differencing).  Algorithmic bytes
+    # per DOF-update of the face stages with RK4 (A subdiagonal, every b_q
+    # non-zero): per stage u^n 32 + Rbar 16 + own records + output state 32,
+    # plus the kept increments K_0..K_2 written once (16 each) and read once by
+    # the last stage (16 each); the inner stages read no earlier K.
+    if rkfr.get("fp32", {}).get("face_update_ms_per_step"):
+        C = 2 * 4 + 1
+        rec = 2 * 2 * (N_DEG + 1) * C * 4 / (N_DEG + 1) ** 2
+        rk_bytes = nodes * (stages * (32 + 16 + rec + 32) + 16 * (stages - 1) * 2)
+        hbm = peaks.get("hbm_gbs")
+        fms, vms = rkfr["fp32"]["face_update_ms_per_step"], rkfr["fp32"]["volume_ms_per_step"]
+        rkfr["fp32"]["face_roofline"] = {"bound": "hbm", "achieved": rk_bytes / (fms * 1e-3) / 1e9, "unit": "GB/s",
+                                         "peak": hbm, "frac": (rk_bytes / (fms * 1e-3) / 1e9 / hbm) if hbm else None,
+                                         "bytes_per_step": rk_bytes}
+        rkfr["fp32"]["volume_roofline"] = {"bound": "alu", "achieved": vflops / (vms * 1e-3) / 1e12,
+                                           "unit": "TFLOP/s", "peak": fp32_peak,
+                                           "frac": vflops / (vms * 1e-3) / 1e12 / fp32_peak}
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -3,8 +3,8 @@
   python -m paper_2604_02125_gb300.run_case --case shear2d --cells 256 256 --N 3 --prec fp32 --steps 3
 
 Cases: wave1d, shear2d, mhd2d, tgv3d; --scheme rkfr runs the multi-stage RKFR
-scheme instead of the single-stage cRKFR step.  Prints the step count, time
-and dt.
+scheme instead of the single-stage cRKFR step, --ncflux stages (mhd2d) the
+stage-wise non-conservative flux.  Prints the step count, time and dt.
 """
 import argparse
 import os
@@ -32,9 +32,11 @@ def main(argv=None):
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--scheme", default="crkfr", choices=["crkfr", "rkfr"])
+    ap.add_argument("--ncflux", default="reduced", choices=["reduced", "stages"])
     a = ap.parse_args(argv)
     build.build()
     mesh, U = CASES[a.case](a.cells, a.N, a.vol)
+    mesh = dict(mesh, ncflux=a.ncflux)
     with crkfr.Solver(mesh, prec=a.prec, scheme=a.scheme) as s:
         s.set_state(U)
         t0 = time.perf_counter()
