@@ -36,9 +36,12 @@ def stages_mesh(N, vol="ec", cells=(5, 7)):
     return dict(mesh, ncflux="stages"), U
 
 
-@pytest.mark.parametrize("N,vol", [(2, "ec"), (3, "ec"), (4, "ec"), (5, "ec"), (3, "central")])
-def test_stagewise_fp64_steps(cr, orc, N, vol):
-    mesh, U = stages_mesh(N, vol)
+@pytest.mark.parametrize("N,vol,cells", [(2, "ec", (5, 7)), (3, "ec", (5, 7)), (4, "ec", (5, 7)), (5, "ec", (5, 7)),
+                                         (3, "central", (5, 7)),
+                                         (3, "ec", (1, 1)),     # one element: its own neighbour on every face
+                                         (2, "ec", (7, 1))])    # one element across y
+def test_stagewise_fp64_steps(cr, orc, N, vol, cells):
+    mesh, U = stages_mesh(N, vol, cells)
     with cr.Solver(mesh, prec="fp64") as s:
         s.set_state(U)
         Uo = U

@@ -7,7 +7,8 @@ b).  Bars as for the single-stage step: FP64 1e-12 relative L2 per step, the
 FP32 pair-flux form 1e-5 after 100 steps, dt equal to the oracle's CFL rule.
 Cases cover every Butcher tableau (N = 1..5), the lane and tile forms of both
 kernels, meshes whose element count is not a multiple of the 32-element tile,
-Euler in 1D/2D/3D and GLM-MHD.
+the degenerate meshes of one element (its own periodic neighbour) and of one
+element across y, Euler in 1D/2D/3D (EC and KEP) and GLM-MHD.
 """
 import numpy as np
 import pytest
@@ -32,7 +33,8 @@ def rel(a, b):
 
 
 def case(name):
-    """(mesh, U) of a small seeded case; element counts 35, 36, 37 (ragged tiles)."""
+    """(mesh, U) of a small seeded case: 35, 36 or 37 elements (ragged tiles), or
+    a degenerate mesh (one element, or one element across y)."""
     kind, N = name.rsplit("_N", 1)
     N = int(N)
     if kind == "euler1d":
@@ -44,11 +46,25 @@ def case(name):
         return inputs.tgv_3d(cells=(3, 3, 4), N=N, mach=0.3)
     if kind == "mhd2d":
         return inputs.mhd_vortex_2d(cells=(5, 7), N=N)
+    if kind == "kep2d":
+        return inputs.shear_layer_2d(cells=(6, 5), N=N, vol="kep")
+    if kind == "single2d":      # one element: its own periodic neighbour in both directions
+        mesh = inputs.mesh_dict("euler", 2, N, [1, 1], [0, 0], [1.0, 1.0], 1.4)
+        return mesh, inputs.smooth_random_field(mesh, seed=50 + N, amp=0.2)
+    if kind == "single1d":
+        mesh = inputs.mesh_dict("euler", 1, N, [1], [0], [2.0], 1.4, cfl=inputs.default_cfl(N))
+        return mesh, inputs.smooth_random_field(mesh, seed=60 + N, amp=0.2)
+    if kind == "strip2d":       # one element across y
+        mesh = inputs.mesh_dict("euler", 2, N, [37, 1], [0, 0], [2.0, 0.1], 1.4)
+        return mesh, inputs.smooth_random_field(mesh, seed=70 + N, amp=0.2)
+    if kind == "singlemhd":
+        return inputs.mhd_vortex_2d(cells=(1, 1), N=N)
     raise ValueError(name)
 
 
 CASES = ["euler1d_N1", "euler1d_N2", "euler1d_N3", "euler1d_N4", "euler1d_N5", "shear2d_N3", "shear2d_N4",
-         "tgv3d_N2", "tgv3d_N4", "mhd2d_N3", "mhd2d_N5"]
+         "tgv3d_N2", "tgv3d_N4", "mhd2d_N3", "mhd2d_N5", "kep2d_N3", "single2d_N3", "single1d_N5", "strip2d_N2",
+         "singlemhd_N3"]
 
 
 @pytest.mark.parametrize("name", CASES)
