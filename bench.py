@@ -169,6 +169,71 @@ def cpu_baseline(sample_cells=(128, 128), steps=6):
                       % (steps, sample_cells[0], sample_cells[1], N_DEG, nodes, dtw)}
 
 
+def _oracle_part(args):
+    """Worker of the all-cores oracle timing: the oracle's restricted step
+    (or_step_elements, the full step's routines on the selected elements and
+    their neighbours) for elements [e_lo, e_hi), read from and written to
+    shared memory."""
+    from multiprocessing import shared_memory
+    import oracle
+    name_in, name_out, shape, mesh, dt, e_lo, e_hi = args
+    si, so = shared_memory.SharedMemory(name=name_in), shared_memory.SharedMemory(name=name_out)
+    try:
+        U = np.ndarray(shape, dtype=np.float64, buffer=si.buf)
+        out = np.ndarray(shape, dtype=np.float64, buffer=so.buf)
+        out[:, e_lo:e_hi, :] = oracle.step_elements(mesh, U, dt, np.arange(e_lo, e_hi))
+    finally:
+        si.close()
+        so.close()
+    return e_hi - e_lo
+
+
+def oracle_parallel_steps(mesh, U, steps, workers):
+    """`steps` oracle steps of (mesh, U) on `workers` processes (spawned: safe
+    after CUDA use), each advancing a contiguous range of elements with the
+    unchanged oracle; dt from the oracle's CFL rule on each step's state.
+    Returns (U after the steps, seconds of the steps without the pool start)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import oracle
+    oracle.build()
+    E = U.shape[1]
+    bounds = np.linspace(0, E, workers + 1).astype(int)
+    bufs = [shared_memory.SharedMemory(create=True, size=U.nbytes) for _ in range(2)]
+    try:
+        arrs = [np.ndarray(U.shape, dtype=np.float64, buffer=b.buf) for b in bufs]
+        arrs[0][...] = U
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_oracle_part, [(bufs[0].name, bufs[1].name, U.shape, mesh, 0.0, 0, 1)])   # start the workers
+            t0 = time.perf_counter()
+            cur = 0
+            for _ in range(steps):
+                dt = oracle.cfl_dt(mesh, arrs[cur])
+                pool.map(_oracle_part, [(bufs[cur].name, bufs[1 - cur].name, U.shape, mesh, dt, int(bounds[k]),
+                                         int(bounds[k + 1])) for k in range(workers) if bounds[k + 1] > bounds[k]])
+                cur = 1 - cur
+            el = time.perf_counter() - t0
+        return arrs[cur].copy(), el
+    finally:
+        for b in bufs:
+            b.close()
+            b.unlink()
+
+
+def cpu_baseline_all_cores(steps=4):
+    """The oracle, as it stands, on every host core: the full 256^2 workload,
+    elements split into contiguous ranges across worker processes."""
+    from paper_2604_02125_gb300 import inputs
+    workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    mesh, U = inputs.shear_layer_2d(cells=CELLS, N=N_DEG)
+    _, el = oracle_parallel_steps(mesh, U, steps, workers)
+    nodes = inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
+    return {"value": nodes * steps / el, "unit": "DOF-updates/s", "cores": workers, "kind": "oracle",
+            "sample": "%d steps of the full %dx%d N=%d workload (%d nodes) on %d processes, each the unchanged "
+                      "oracle's restricted step on a contiguous range of elements, %.1f s"
+                      % (steps, CELLS[0], CELLS[1], N_DEG, nodes, workers, el)}
+
+
 def run_batched(crkfr, inputs, stream, steps):
     """512 independent 2D Euler solves (sides 16..128, N in 2..5, FP32 pair
     fluxes, FP64 update) advanced together; per-step CUDA events on the
@@ -506,6 +571,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
