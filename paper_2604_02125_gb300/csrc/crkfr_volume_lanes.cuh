@@ -155,6 +155,64 @@ __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2
 }
 
 
+// Flux differencing of one line of the element at `my`, rolled over the pairs
+// so that the two-point flux is compiled once: pair data read from shared
+// memory (Q, component c at Q[c * NP + node]) in the frame of swap_xy when
+// sw is set, the residual (times inv_dx) added into shared memory (RY, in the
+// element's own frame); the end nodes' pair data and fluxes are returned for
+// the face sums.  Every node of the line belongs to the calling thread.
+template <class EQ, int N, typename R>
+__device__ __forceinline__ void line_residual_rolled(const R* __restrict__ Q, R* __restrict__ RY, int NPv, int base,
+                                                     int stride, bool sw, R (&qe)[N + 1][EQ::P], R (&fend)[2][EQ::M],
+                                                     const PhysParams<R>& pp, const RefTab<R>& tb, R inv_dx) {
+  constexpr int n = N + 1, M = EQ::M, P = EQ::P;
+  auto load = [&](int node, R* q) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) q[c] = Q[(sw ? swap_xy<EQ>(c) : c) * NPv + node];
+  };
+  load(base, qe[0]);
+  load(base + N * stride, qe[N]);
+  EQ::flux(0, qe[0], fend[0], pp);
+  EQ::flux(0, qe[N], fend[1], pp);
+#pragma unroll 1
+  for (int a = 0; a < n; ++a) {
+    const int na = base + a * stride;
+    R qa[P], acc[M];
+    load(na, qa);
+    // D_aa f(q_a): non-zero only at the two end points of a GLL line
+    const R caa = R(2) * tb.D[a][a] * inv_dx;
+#pragma unroll
+    for (int v = 0; v < M; ++v) acc[v] = a == 0 ? caa * fend[0][v] : (a == N ? caa * fend[1][v] : R(0));
+#pragma unroll 1
+    for (int b = a + 1; b < n; ++b) {
+      const int nb = base + b * stride;
+      R qb[P], f[M];
+      load(nb, qb);
+      EQ::two_point(0, qa, qb, f, pp);
+      const R cab = R(2) * tb.D[a][b] * inv_dx, cba = R(2) * tb.D[b][a] * inv_dx;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        acc[v] += cab * f[v];
+        RY[(sw ? swap_xy<EQ>(v) : v) * NPv + nb] += cba * f[v];
+      }
+    }
+    if constexpr (EQ::NC) {
+      // sum_b D_ab B(u_a) g(u_b) = B(u_a) (D g)_a (no factor 2)
+      R dg[2] = {R(0), R(0)};
+#pragma unroll 1
+      for (int b = 0; b < n; ++b) {
+        const int nb = base + b * stride;
+        const R dab = tb.D[a][b] * inv_dx;
+        dg[0] += dab * Q[(sw ? swap_xy<EQ>(EQ::IB) : EQ::IB) * NPv + nb];
+        dg[1] += dab * Q[EQ::IPSI * NPv + nb];
+      }
+      EQ::nc_apply(0, qa, dg, acc);
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) RY[(sw ? swap_xy<EQ>(v) : v) * NPv + na] += acc[v];
+  }
+}
+
 // Time averages at the two end points of one line in direction D (the face
 // nodes of the two faces normal to D): U = sum_i b_i u^(i), F^D = sum_i b_i
 // f^D(u^(i)) (eq. disc.avg.flux), lambda_D(u^n), and for the non-conservative
@@ -328,7 +386,15 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   // across the barrier.  Measured: degree 5 (FP32) 244 against 254 us and the
   // GLM-MHD vortex at degree 4 (FP64) 4.71 against 4.86 ms per launch, but
   // degree 4 (FP32) 211 against 194 us; elsewhere no gain.
-  constexpr bool ROLL = !L::PACK && DIM == 2 && (N >= 5 || (EQ::NC && sizeof(R) == 8));
+  constexpr bool ROLL = !L::PACK && DIM == 2 && (N >= 5 || (EQ::NC && sizeof(R) == 8)) && !(EQ::NC && sizeof(R) == 4 && N >= 4);
+  // 2D GLM-MHD in FP32 at degree 4 and 5: the pair loop itself rolled
+  // (line_residual_rolled), both directions' residuals added in place into the
+  // shared buffer RY (cleared by the node phase), so the x-line residual is not
+  // held in registers either.  Measured per launch: degree 5 (96^2) 520 against
+  // 600 us, degree 4 (128^2) 542 against 569 us; degree 3 slower (110 against
+  // 87 us), so it keeps the form below.
+  constexpr bool ROLLP = !L::PACK && DIM == 2 && EQ::NC && sizeof(R) == 4 && N >= 4;
+  constexpr bool ONEQ = ROLL || ROLLP;   // the node phase keeps no pair data
   constexpr int NS = rk_nsaved(N) > 0 ? rk_nsaved(N) : 1;
 
   const int tid = threadIdx.x;
@@ -372,7 +438,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   for (int i = 0; i < S; ++i) {
     const R bi = S1 ? R(1) : tb.b[i];
     // ---------------- node phase (own x-line): stage state and pair data
-    R q[ROLL ? 1 : n][P];
+    R q[ONEQ ? 1 : n][P];
     if (active) {
 #pragma unroll
       for (int k = 0; k < n; ++k) {
@@ -382,8 +448,9 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         for (int v = 0; v < M; ++v) {
           R acc = R(0);
           if (i > 0) {
-            // complete R_{i-1} = x part (registers) + y/z part (shared)
-            R r = ax[k][v] + (DIM > 1 ? my[L::O_RY + v * NP + p] : R(0));
+            // complete R_{i-1} = x part (registers) + y/z part (shared); the
+            // rolled-pair form keeps both in shared memory
+            R r = (ROLLP ? R(0) : ax[k][v]) + (DIM > 1 ? my[L::O_RY + v * NP + p] : R(0));
             rb[k][v] += tb.b[i - 1] * r;
             acc = tb.a[i][i - 1] * r;
             if constexpr (rk_nsaved(N) > 0) {
@@ -393,14 +460,15 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
             }
           }
           uu[v] = my[L::O_U0 + v * NP + p] - dtR * acc;
+          if constexpr (ROLLP) my[L::O_RY + v * NP + p] = R(0);
         }
-        R* qk = q[ROLL ? 0 : k];
+        R* qk = q[ONEQ ? 0 : k];
         EQ::pair_data(uu, qk, pp);
         if (DIM > 1) {
 #pragma unroll
           for (int c = 0; c < P; ++c) my[L::O_Q + c * NP + p] = qk[c];
         }
-        if constexpr (ROLL && EQ::NCS) {
+        if constexpr (ONEQ && EQ::NCS) {
           // face traces of this stage: the ends of the x-line, and the whole
           // x-line where it lies on a face normal to y
           if (k == 0) write_stage_prims<EQ, N, R>(trace, 0, 0, l, i, E, e0 + el, qk);
@@ -409,7 +477,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
           if (l == N) write_stage_prims<EQ, N, R>(trace, 1, 1, k, i, E, e0 + el, qk);
         }
       }
-      if constexpr (EQ::NCS && !ROLL) {
+      if constexpr (EQ::NCS && !ONEQ) {
         // face traces of this stage at the ends of the x-line (stage-wise
         // non-conservative flux)
         write_stage_prims<EQ, N, R>(trace, 0, 0, l, i, E, e0 + el, q[0]);
@@ -417,7 +485,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
       }
       // ---------------- x-direction flux differencing, all in registers
       // (packed form: together with the y-line below)
-      if constexpr (!PACK && !ROLL) {
+      if constexpr (!PACK && !ONEQ) {
         R fend[2][M];
         line_residual<EQ, N, R, 0>(q, ax, fend, pp, tb, inv_dx_of<R>(ma, 0));
         face_accumulate<EQ, N, R, 0>(fx, q, fend, bi, i == 0, pp);
@@ -457,6 +525,21 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         face_accumulate<EQ, N, R, 1>(fy, qy, fey, bi, i == 0, pp);
       }
       __syncthreads();   // RY complete
+    } else if constexpr (ROLLP) {
+      __syncthreads();   // Q of this stage visible; RY of the last stage consumed and cleared
+#pragma unroll 1
+      for (int dir = 0; dir < 2; ++dir) {
+        if (active) {
+          R qe[n][P], fe[2][M];
+          line_residual_rolled<EQ, N, R>(my + L::O_Q, my + L::O_RY, NP, dir ? l : l * n, dir ? n : 1, dir != 0, qe,
+                                         fe, pp, tb, dir ? inv_dx_of<R>(ma, 1) : inv_dx_of<R>(ma, 0));
+          if (dir == 0) face_accumulate<EQ, N, R, 0>(fx, qe, fe, bi, i == 0, pp);
+          else face_accumulate<EQ, N, R, 0>(fy, qe, fe, bi, i == 0, pp);   // swapped frame
+        }
+        // the x pass is complete before the y pass adds into the same nodes;
+        // after the y pass RY holds the whole residual
+        __syncthreads();
+      }
     } else if constexpr (ROLL) {
       __syncthreads();   // Q of this stage visible; RY of the last stage consumed
       if (active) {
@@ -538,7 +621,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
       const int p = l * n + k;
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        R r = ax[k][v] + (DIM > 1 ? my[L::O_RY + v * NP + p] : R(0));
+        R r = (ROLLP ? R(0) : ax[k][v]) + (DIM > 1 ? my[L::O_RY + v * NP + p] : R(0));
         my[L::O_Q + v * NP + p] = rb[k][v] + (S1 ? R(1) : tb.b[S - 1]) * r;
       }
     }
@@ -559,7 +642,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     // end nodes: x-line l (l n, l n + N), y-line l (by, by + N n), z-line l (l, l + N n^2)
     const int by = (l % n) + (l / n) * n * n;
     write_records<EQ, R, NF>(trace, fx, 0, E, e0 + el, l, u0 + l * n, u0 + l * n + N, NP);
-    if constexpr (ROLL) {
+    if constexpr (ONEQ) {
       FaceAcc<EQ, R> fyo;
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
