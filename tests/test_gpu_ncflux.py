@@ -62,7 +62,7 @@ def test_stagewise_fp64_steps(cr, orc, N, vol, cells):
     assert rel(G, red) > 1e3 * rel(G, orc.step(mesh, U, orc.cfl_dt(mesh, U)))
 
 
-@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("N", [3, 4, 5])
 def test_stagewise_fp32_100_steps(cr, orc, N):
     mesh, U = stages_mesh(N)
     with cr.Solver(mesh, prec="fp32") as s:

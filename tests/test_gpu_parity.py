@@ -104,7 +104,8 @@ def test_fp64_free_run(cr, orc, name):
 
 
 @pytest.mark.parametrize("name,steps", [("wave1d_N3", 100), ("shear2d_N3", 100), ("mhd2d_N4", 100),
-                                        ("tgv3d_N3", 100), ("smooth2d_N5", 100), ("smooth2d_N2", 100)])
+                                        ("mhd2d_N5", 100), ("mhd2d_N3", 100), ("tgv3d_N3", 100),
+                                        ("smooth2d_N5", 100), ("smooth2d_N2", 100), ("smooth2d_N4", 100)])
 def test_fp32_pairflux_error(cr, orc, name, steps):
     mesh, U = _case(name)
     ref, dts = orc.run(mesh, U, steps)

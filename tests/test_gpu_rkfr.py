@@ -86,7 +86,7 @@ def test_rkfr_fp64_steps(cr, orc, name):
     assert tun["scheme"] == "rkfr"
 
 
-@pytest.mark.parametrize("name", ["euler1d_N5", "shear2d_N3", "tgv3d_N2", "mhd2d_N3"])
+@pytest.mark.parametrize("name", ["euler1d_N5", "shear2d_N3", "shear2d_N4", "tgv3d_N2", "mhd2d_N3", "mhd2d_N5"])
 def test_rkfr_fp32_100_steps(cr, orc, name):
     mesh, U = case(name)
     with cr.Solver(mesh, prec="fp32", scheme="rkfr") as s:
