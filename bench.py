@@ -291,6 +291,9 @@ ORACLE_SAMPLES = {
     "shear2d_256_N3_central": ("shear_layer_2d", dict(cells=(32, 32), N=3, vol="central"), 40),
     "mhd2d_128_N4": ("mhd_vortex_2d", dict(cells=(16, 16), N=4), 40),
     "tgv3d_64_N3": ("tgv_3d", dict(cells=(8, 8, 8), N=3), 20),
+    # the multi-stage RKFR scheme and the stage-wise non-conservative flux
+    "shear2d_256_N3_rkfr": ("shear_layer_2d", dict(cells=(32, 32), N=3), 40, "rkfr"),
+    "mhd2d_128_N4_ncstages": ("mhd_vortex_2d", dict(cells=(16, 16), N=4), 40, "ncstages"),
 }
 
 
@@ -299,11 +302,16 @@ def cpu_baseline_configs():
     import oracle
     from paper_2604_02125_gb300 import inputs
     oracle.build()
-    for name, (fn, kw, steps) in ORACLE_SAMPLES.items():
+    for name, (fn, kw, steps, *variant) in ORACLE_SAMPLES.items():
         mesh, U = getattr(inputs, fn)(**kw)
+        step = oracle.step
+        if variant == ["rkfr"]:
+            step = oracle.rkfr_step
+        elif variant == ["ncstages"]:
+            mesh = dict(mesh, ncflux="stages")
         t0 = time.perf_counter()
         for _ in range(steps):
-            U = oracle.step(mesh, U, oracle.cfl_dt(mesh, U))
+            U = step(mesh, U, oracle.cfl_dt(mesh, U))
         el = time.perf_counter() - t0
         nodes = inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
         print(json.dumps({"workload": name, "kind": "oracle", "cores": 1, "dof_updates_per_s": nodes * steps / el,
