@@ -62,7 +62,10 @@ def build(force=False, verbose=False, jobs=None):
     if todo:
         with cf.ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
             list(ex.map(compile_one, todo))
-    if todo or not os.path.exists(LIB) or force:
+    # relink when anything was compiled, and whenever the library is older than
+    # an object (a link that failed after compiling must not leave an old one)
+    stale_lib = not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if todo or stale_lib or force:
         cmd = [nvcc, "-gencode", GENCODE, "-shared", "-o", LIB + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
