@@ -254,7 +254,7 @@ static bool desc_valid(const cr_mesh_desc& d) {
   if (d.ncflux != CR_NCFLUX_REDUCED &&
       (d.ncflux != CR_NCFLUX_STAGES || d.eq != CR_GLM_MHD || d.scheme != CR_SCHEME_CRKFR))
     return false;
-  if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || d.dt_fixed < 0.0 || !(d.c_h >= 0.0)) return false;
+  if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || !(d.dt_fixed >= 0.0) || !(d.c_h >= 0.0)) return false;   // NaN fails
   for (int k = 0; k < d.dim; ++k) {
     if (d.cells[k] < 1) return false;
     if (!(d.hi[k] > d.lo[k])) return false;

@@ -8,7 +8,9 @@ GLL point positions come from numpy's Legendre routines, and the only physics
 is the conversion of primitive initial data to conserved variables.
 
 Mesh dict keys: eq ('euler' | 'glm_mhd'), dim, N, cells, lo, hi, gamma, cfl,
-c_h, vol ('ec' | 'kep' | 'central'), surf ('rusanov').
+c_h, vol ('ec' | 'kep' | 'central'), surf ('rusanov'); optional, read by the
+library binding and the oracle: scheme ('crkfr' | 'rkfr'), ncflux ('reduced' |
+'stages', GLM-MHD).
 
 Workloads (the paper's own test cases need a limiter or equations that are not
 printed, so these smooth periodic problems stand in for them):

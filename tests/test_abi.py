@@ -88,7 +88,8 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
         assert _init_status(lib, m) == crkfr.CR_EINVAL, m
     d = crkfr.make_desc(base)
     h = ctypes.c_void_p()
-    for field, value in (("surf", 1), ("prec", 2), ("vol", 3), ("dt_fixed", -1.0), ("scheme", 2), ("scheme", -1),
+    for field, value in (("surf", 1), ("prec", 2), ("vol", 3), ("dt_fixed", -1.0), ("dt_fixed", float("nan")),
+                         ("gamma", float("nan")), ("cfl", float("nan")), ("c_h", float("nan")), ("scheme", 2), ("scheme", -1),
                          ("ncflux", 2), ("ncflux", 1)):           # the stage-wise flux is for GLM-MHD only
         d2 = crkfr.make_desc(base)
         setattr(d2, field, value)
@@ -118,3 +119,55 @@ def test_noalloc_size_limit_without_gpu(lib):
                               ncflux="stages"))
     assert lib.cr_step_noalloc(ctypes.byref(ns), dummy, dummy, None, None) == crkfr.CR_EINVAL
     assert lib.cr_step_noalloc(None, dummy, dummy, None, None) == crkfr.CR_EINVAL
+
+
+def _valid(d):
+    """The descriptor rules of include/cr.h (cr_init_mesh), restated."""
+    import math
+    if d.eq not in (0, 1) or not (1 <= d.dim <= 3) or not (1 <= d.degree_N <= 5):
+        return False
+    if d.eq == 1 and (d.dim != 2 or d.vol == 1):
+        return False
+    if d.vol not in (0, 1, 2) or d.surf != 0 or d.prec not in (0, 1) or d.scheme not in (0, 1):
+        return False
+    if d.ncflux != 0 and (d.ncflux != 1 or d.eq != 1 or d.scheme != 0):
+        return False
+    if not (d.gamma > 1.0) or not (d.cfl > 0.0) or not (d.dt_fixed >= 0.0) or not (d.c_h >= 0.0):
+        return False
+    nodes = 1
+    for k in range(d.dim):
+        if d.cells[k] < 1 or not (d.hi[k] > d.lo[k]) or math.isnan(d.hi[k] - d.lo[k]):
+            return False
+        nodes *= d.cells[k] * (d.degree_N + 1)
+    return nodes < 2 ** 31
+
+
+def test_random_descriptors_rejected_without_gpu(lib):
+    """Seeded random descriptors: every one that breaks a documented rule is
+    CR_EINVAL before any CUDA call, and none crashes the library.  (Descriptors
+    that satisfy every rule are not passed in: on a GPU machine they would
+    allocate.)"""
+    import numpy as np
+    from paper_2604_02125_gb300 import crkfr
+    rng = np.random.default_rng(20261203)
+    h = ctypes.c_void_p()
+    pick = lambda vals: vals[int(rng.integers(len(vals)))]   # noqa: E731
+    tried = 0
+    for _ in range(3000):
+        d = crkfr.MeshDesc()
+        d.eq, d.dim, d.degree_N = pick([0, 1, 2, -1]), pick([0, 1, 2, 3, 4]), pick([0, 1, 3, 5, 6])
+        for k in range(3):
+            d.cells[k] = pick([-1, 0, 1, 7, 65536])
+            d.lo[k] = pick([0.0, -1.0, float("nan")])
+            d.hi[k] = pick([1.0, 0.0, -2.0, float("inf")])
+        d.gamma, d.cfl = pick([1.4, 1.0, 0.5, float("nan")]), pick([0.1, 0.0, -1.0, float("nan")])
+        d.c_h, d.dt_fixed = pick([0.0, 1.0, -1.0, float("nan")]), pick([0.0, 1e-3, -1.0, float("nan")])
+        d.vol, d.surf, d.prec = pick([0, 1, 2, 3]), pick([0, 1]), pick([0, 1, 2])
+        d.scheme, d.ncflux = pick([0, 1, 2]), pick([0, 1, 2])
+        if _valid(d):
+            continue
+        tried += 1
+        assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d), 1, None) == crkfr.CR_EINVAL, (
+            [getattr(d, f) for f, _ in d._fields_ if f not in ("cells", "lo", "hi")])
+        assert not h.value
+    assert tried > 2500
