@@ -210,9 +210,12 @@ int cr_check_conversions(long long n, unsigned long long seed, long long *mismat
  * device array of CR_NOALLOC_SCRATCH_BYTES per device, held until the
  * process exits; a mesh needing more returns CR_ETOOLARGE (roughly 80k nodes
  * of 2D Euler in FP64).  The first call on a device looks up that array's
- * device address, so make it before any stream capture.  Every call shares
- * the array: calls that overlap on the GPU race.  Physicality is not
- * reported; use the regular entry points for status. */
+ * device address and keeps it for the life of the process, so make it before
+ * any stream capture, and do not call this entry point on a device after
+ * cudaDeviceReset (the address belonged to the destroyed context).  Every
+ * call shares the array: calls that overlap on the GPU race.  Physicality is
+ * not reported; use the regular entry points for status.  Device pointers of
+ * the wrong size are not detected (the sizes follow from desc). */
 #define CR_NOALLOC_SCRATCH_BYTES (8u << 20)
 int cr_step_noalloc(const cr_mesh_desc *desc, const double *u_in, double *u_out, double *dt_out,
                     void *cuda_stream);

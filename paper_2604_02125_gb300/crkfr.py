@@ -251,15 +251,33 @@ def step_noalloc(mesh, u_in, u_out, dt_out=None, prec="fp64", dt_fixed=0.0, stre
     scratch is the library's static per-device array.  u_in, u_out (and dt_out,
     a 1-element float64 tensor) are CUDA tensors; u_out may be u_in.  Returns
     the C status (raises CrError on failure)."""
+    import torch
     lib = load_library()
     d = make_desc(mesh, prec, dt_fixed)
     if stream is None:
         stream = _current_torch_stream()
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    for t in (u_in, u_out) + ((dt_out,) if dt_out is not None else ()):
-        if not getattr(t, "is_cuda", False):
-            raise ValueError("cr_step_noalloc takes device tensors")
+    # the C entry point takes raw device pointers and trusts their sizes: check
+    # type, layout, size and device here, before any kernel can touch them
+    from . import inputs
+    need = inputs.nvars(mesh) * inputs.num_elems(mesh) * inputs.nodes_per_elem(mesh)
+    dev = torch.cuda.current_device()
+    for name, t in (("u_in", u_in), ("u_out", u_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("cr_step_noalloc: %s must be a CUDA tensor" % name)
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("cr_step_noalloc: %s must be contiguous float64" % name)
+        if t.numel() != need:
+            raise ValueError("cr_step_noalloc: %s has %d values, the mesh needs %d" % (name, t.numel(), need))
+        if t.device.index != dev:
+            raise ValueError("cr_step_noalloc: %s is on cuda:%s, the current device is cuda:%d"
+                             % (name, t.device.index, dev))
+    if dt_out is not None:
+        if (not isinstance(dt_out, torch.Tensor) or not dt_out.is_cuda or dt_out.dtype != torch.float64
+                or dt_out.numel() < 1 or dt_out.device.index != dev):
+            raise ValueError("cr_step_noalloc: dt_out must be a float64 CUDA tensor of at least one value "
+                             "on the current device")
     rc = lib.cr_step_noalloc(ctypes.byref(d), ctypes.c_void_p(u_in.data_ptr()), ctypes.c_void_p(u_out.data_ptr()),
                              ctypes.c_void_p(dt_out.data_ptr()) if dt_out is not None else None,
                              ctypes.c_void_p(int(stream or 0)))

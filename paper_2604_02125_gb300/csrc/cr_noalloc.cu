@@ -14,7 +14,10 @@
 // process exits.  All calls on a device share it and it keeps the last call's
 // contents, so calls that overlap on the GPU (on different streams, or from
 // several threads) race; the step record is cleared at the start of every
-// call.
+// call.  The array's device address is looked up on the first call on each
+// device and kept for the life of the process; cudaDeviceReset destroys the
+// context that address belongs to, so a process that resets a device must
+// not call this entry point on that device afterwards.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -123,7 +126,7 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
   lc.sms = 1;
-  cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return to_status(e);
   lc.ma.tma_ok = tma_ok_for(u_out, E, o.NP);
 
   if ((e = o.set_smem(o.vol_smem(lc.epb))) != cudaSuccess) return to_status(e);

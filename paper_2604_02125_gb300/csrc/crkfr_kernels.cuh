@@ -568,6 +568,8 @@ __device__ __forceinline__ void face_update_body(double* __restrict__ u, const R
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM);
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
+  // a volume CTA that timed out left its records unwritten: leave u^n as it is
+  if (st->status & ST_TIMEOUT) return;
   const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
   R lam = R(0);
   bool bad = false;

@@ -711,7 +711,12 @@ __device__ __forceinline__ void volume_lanes_persistent(const double* __restrict
     if (staged) {
       const bool ok = mbar_wait_bounded(bar, phase);
       if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicOr(&st->status, ST_TIMEOUT);
+        // the copy may still be in flight: thread 0 waits for it once more
+        // (bounded) before the CTA's shared memory is released
+        if (threadIdx.x == 0) {
+          atomicOr(&st->status, ST_TIMEOUT);
+          mbar_wait_bounded(bar, phase);
+        }
         return;
       }
       phase ^= 1u;
@@ -830,6 +835,8 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   const int tid = threadIdx.x;
   const int l = tid >> 5, el = tid & 31;
   const long long E = ma.E;
+  // a volume CTA that timed out left its records unwritten: leave u^n as it is
+  if (st->status & ST_TIMEOUT) return;
   const bool active = (long long)e0 + el < E;
   const unsigned e = e0 + el;
   const R dtR = step_dt<R>(st);
@@ -1025,7 +1032,10 @@ k_volume_batched(const BatchSolve* __restrict__ solves, const BatchTile* __restr
     if (staged) {
       const bool ok = mbar_wait_bounded(bar, phase);
       if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicOr(&bs.st->status, ST_TIMEOUT);
+        if (threadIdx.x == 0) {
+          atomicOr(&bs.st->status, ST_TIMEOUT);
+          mbar_wait_bounded(bar, phase);
+        }
         return;
       }
       phase ^= 1u;

@@ -2,13 +2,15 @@
 
 Bars: FP64 path <= 1e-12 relative L2 per step from an identical state (and
 over short free runs), dt identical to 1e-14; FP32 pair-flux form <= 1e-5
-relative L2 after 100 steps on smooth data.  Sizes span several CTAs of the
-volume kernel with a ragged tail of elements.
+relative L2 after 100 steps on smooth data.  Every comparison also bounds the
+per-variable largest nodal difference by the same tolerance (parity_util).
+Sizes span several CTAs of the volume kernel with a ragged tail of elements.
 """
 import numpy as np
 import pytest
 
 from paper_2604_02125_gb300 import inputs
+from parity_util import check_close
 
 pytestmark = pytest.mark.gpu
 
@@ -48,9 +50,15 @@ def _case(name):
         return inputs.tgv_3d(cells=(4, 3, 5), N=3, mach=0.3)
     if name == "tgv3d_N2":
         return inputs.tgv_3d(cells=(3, 4, 3), N=2, mach=0.3)
-    if name.startswith("mhd2d_N"):
+    if name in ("tgv3d_N1", "tgv3d_N4", "tgv3d_N5"):
+        # 3D N = 4, 5: the tile-form volume kernel (the lane layout does not fit);
+        # N = 5: the per-node face / update kernel
         N = int(name[-1])
-        return inputs.mhd_vortex_2d(cells=(6, 5), N=N)
+        return inputs.tgv_3d(cells=(3, 4, 3) if N < 5 else (3, 2, 3), N=N, mach=0.3, cfl=inputs.default_cfl(N))
+    if name.startswith("mhd2d_N"):
+        # N = 5 in FP64: the tile-form volume kernel
+        N = int(name[-1])
+        return inputs.mhd_vortex_2d(cells=(6, 5) if N < 5 else (7, 5), N=N, cfl=inputs.default_cfl(N))
     if name == "mhd2d_central":
         return inputs.mhd_vortex_2d(cells=(5, 5), N=3, vol="central")
     if name == "single2d_N3":   # one element: its own periodic neighbour in both directions
@@ -67,7 +75,8 @@ def _case(name):
 
 FP64_CASES = ["wave1d_N3", "wave1d_N1", "wave1d_N2", "wave1d_N4", "wave1d_N5", "shear2d_N3", "shear2d_N3_kep",
               "smooth2d_N1", "smooth2d_N2", "smooth2d_N4", "smooth2d_N5", "central2d_N3", "tgv3d_N3", "tgv3d_N2",
-              "mhd2d_N3", "mhd2d_N4", "mhd2d_N2", "mhd2d_central", "single2d_N3", "single1d_N5", "strip2d_N2"]
+              "mhd2d_N3", "mhd2d_N4", "mhd2d_N2", "mhd2d_central", "single2d_N3", "single1d_N5", "strip2d_N2",
+              "tgv3d_N1", "tgv3d_N4", "tgv3d_N5", "mhd2d_N1", "mhd2d_N5"]
 
 
 @pytest.mark.parametrize("name", FP64_CASES)
@@ -83,8 +92,7 @@ def test_fp64_per_step_parity(cr, orc, name):
             info = s.info()
             assert abs(info["dt"] - dt) <= 1e-14 * dt, (info["dt"], dt)
             assert info["steps"] == 1
-            err = rel(out, ref)
-            assert err <= 1e-12, (name, k, err)
+            check_close(out, ref, 1e-12, (name, k))
             U = ref
 
 
@@ -100,12 +108,15 @@ def test_fp64_free_run(cr, orc, name):
         info = s.info()
     assert info["steps"] == nsteps
     assert abs(info["t"] - sum(dts)) <= 1e-12 * sum(dts)
-    assert rel(out, ref) <= 1e-12, rel(out, ref)
+    check_close(out, ref, 1e-12, name)
 
 
 @pytest.mark.parametrize("name,steps", [("wave1d_N3", 100), ("shear2d_N3", 100), ("mhd2d_N4", 100),
                                         ("mhd2d_N5", 100), ("mhd2d_N3", 100), ("tgv3d_N3", 100),
-                                        ("smooth2d_N5", 100), ("smooth2d_N2", 100), ("smooth2d_N4", 100)])
+                                        ("smooth2d_N5", 100), ("smooth2d_N2", 100), ("smooth2d_N4", 100),
+                                        ("tgv3d_N4", 100), ("tgv3d_N5", 100), ("tgv3d_N1", 100),
+                                        ("mhd2d_N1", 100), ("wave1d_N1", 100), ("wave1d_N5", 100),
+                                        ("smooth2d_N1", 100), ("tgv3d_N2", 100), ("mhd2d_N2", 100)])
 def test_fp32_pairflux_error(cr, orc, name, steps):
     mesh, U = _case(name)
     ref, dts = orc.run(mesh, U, steps)
@@ -113,8 +124,7 @@ def test_fp32_pairflux_error(cr, orc, name, steps):
         s.set_state(U)
         s.step(steps)
         out = s.get_state()
-    err = rel(out, ref)
-    assert err <= 1e-5, (name, err)
+    check_close(out, ref, 1e-5, name)
 
 
 @pytest.mark.parametrize("name,cons", [("shear2d_N3", range(4)), ("tgv3d_N3", range(5)), ("mhd2d_N4", [0])])
@@ -189,7 +199,7 @@ def test_fixed_dt_and_time(cr, orc):
         out = s.get_state()
     ref, _ = orc.run(mesh, U, 7, dt_fixed=1e-3)
     assert info["dt"] == 1e-3 and abs(info["t"] - 7e-3) < 1e-15
-    assert rel(out, ref) < 1e-12
+    check_close(out, ref, 1e-12)
 
 
 def test_device_pointers_and_torch_stream(cr, orc):
@@ -205,7 +215,7 @@ def test_device_pointers_and_torch_stream(cr, orc):
             s.set_state(Ud)
             s.step(1)
             s.get_state(out)
-    assert rel(out.cpu().numpy(), ref) < 1e-12
+    check_close(out.cpu().numpy(), ref, 1e-12)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
