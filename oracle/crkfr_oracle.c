@@ -69,6 +69,10 @@ typedef struct {
                       1 = sum_j b_j B(u^{(j),+-}) g^avg(u^(j)) (eq. bad.numflux.non.cons)      */
   int tab_s;       /* > 0: use this explicit RK tableau instead of the degree's (tests)   */
   const double *tab_A, *tab_b;   /* [7][7] row-major, [7]                            */
+  int limiter;     /* 1: subcell blending limiter (Sec. 4; Euler, cRKFR step only)       */
+  double alpha_max;    /* cap of the blending coefficient                             */
+  double alpha_fixed;  /* >= 0: this blending coefficient in every element (pins);
+                          < 0: the smoothness indicator decides                        */
 } or_desc;
 
 /* ------------------------------------------------------------------------- */
@@ -594,6 +598,241 @@ static void nc_with_gavg(const or_desc *d, int dir, const double *un_side, const
   nc_product(d, dir, un_side, gavg_state, out);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Subcell blending limiter (Sec. 4: the paper's Kelvin-Helmholtz and         */
+/* Richtmyer-Meshkov runs blend the cRKFR update with a first-order subcell   */
+/* finite-volume update, the coefficient capped by alpha_max; the paper cites */
+/* the method without printing it).  Readings, compressible Euler only:       */
+/*  - subcells: the element line of N+1 GLL points is cut into N+1 subcells   */
+/*    of widths w_p dx (the quadrature weights); subcell p holds node p;      */
+/*  - low-order update: first-order finite volumes with the Rusanov flux of   */
+/*    the two u^n node values at every interior subcell face, forward Euler   */
+/*    in time, per direction summed (tensor product);                        */
+/*  - at an element face both updates take one flux: the blend                */
+/*    (1 - a_f) F^num + a_f f_lo, a_f the mean of the two elements'           */
+/*    coefficients, F^num the time-averaged Rusanov flux of eq. numflux.cons, */
+/*    f_lo the Rusanov flux of the u^n traces; where a_f > 0 it is pulled     */
+/*    toward f_lo (F = f_lo + theta (blend - f_lo)) by the largest theta in   */
+/*    [0,1] for which both adjacent end subcells' one-direction low-order     */
+/*    states keep rho and p above a tenth of their values with f_lo (density  */
+/*    linear, pressure concave in theta);                                    */
+/*  - u^{n+1} = (1 - a_e) u^H + a_e u^L per element (u^L alone where a_e = 1, */
+/*    f_lo alone where a_f = 1);                                             */
+/*  - a_e from the modal smoothness indicator of rho p: energy fraction of    */
+/*    the highest modes in the orthonormal Legendre basis, mapped through a   */
+/*    logistic function with threshold 0.5 10^(-1.8 (N+1)^(1/4)) and         */
+/*    sharpness ln(9999), set to 0 below 0.001 and 1 above 0.999, capped by   */
+/*    alpha_max, then raised to half of the largest face neighbour's value.   */
+/* ------------------------------------------------------------------------- */
+
+/* orthonormal Legendre polynomial sqrt((2j+1)/2) P_j(x) on [-1,1] */
+static double legendre_orthonormal(int j, double x) {
+  double P, dP;
+  legendre(j, x, &P, &dP);
+  return sqrt((2.0 * j + 1.0) / 2.0) * P;
+}
+
+/* Solve A x = b (n <= OR_MAXNP) by Gaussian elimination with partial pivoting;
+ * A (row-major) and b are overwritten, x returned in b. */
+static void solve_dense(int n, double *A, double *b) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A[i * n + k]) > fabs(A[piv * n + k])) piv = i;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) { double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+      double t = b[k]; b[k] = b[piv]; b[piv] = t;
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double f = A[i * n + k] / A[k * n + k];
+      for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double acc = b[k];
+    for (int j = k + 1; j < n; ++j) acc -= A[k * n + j] * b[j];
+    b[k] = acc / A[k * n + k];
+  }
+}
+
+/* Highest-mode energy fraction E of one element's rho p ([node][var] in ue):
+ * modal coefficients m of the tensor-product orthonormal Legendre expansion
+ * interpolating rho p at the nodes (a 1D Vandermonde solve along every
+ * direction), then E = max((T - T1)/T, (T1 - T2)/T1) with T the sum of all
+ * m^2, T1 over the modes of degree <= N-1 in every direction, T2 <= N-2
+ * (the second fraction only for N >= 2). */
+double or_indicator_energy(const or_desc *d, const double *ue) {
+  int n = d->N + 1, dim = d->dim, M = nvars(d);
+  double x[OR_MAXNP];
+  gll_ref_points(d->N, x);
+  int np = 1;
+  for (int k = 0; k < dim; ++k) np *= n;
+  double m[OR_MAXNP * OR_MAXNP * OR_MAXNP];
+  for (int p = 0; p < np; ++p) {
+    double rho, v[3], pr;
+    euler_prim(d, &ue[p * M], &rho, v, &pr);
+    m[p] = rho * pr;
+  }
+  /* along direction k: for every line, solve V c = values (V_pj = phi_j(x_p)) */
+  for (int k = 0; k < dim; ++k) {
+    int stride = 1;
+    for (int j = 0; j < k; ++j) stride *= n;
+    for (int base = 0; base < np; ++base) {
+      if ((base / stride) % n != 0) continue;           /* first node of a line in direction k */
+      double V[OR_MAXNP * OR_MAXNP], b[OR_MAXNP];
+      for (int p = 0; p < n; ++p) {
+        b[p] = m[base + p * stride];
+        for (int j = 0; j < n; ++j) V[p * n + j] = legendre_orthonormal(j, x[p]);
+      }
+      solve_dense(n, V, b);
+      for (int p = 0; p < n; ++p) m[base + p * stride] = b[p];
+    }
+  }
+  double T = 0.0, T1 = 0.0, T2 = 0.0;
+  for (int p = 0; p < np; ++p) {
+    int rem = p, top = 0;
+    for (int k = 0; k < dim; ++k) { int j = rem % n; rem /= n; if (j > top) top = j; }
+    double e2 = m[p] * m[p];
+    T += e2;
+    if (top <= d->N - 1) T1 += e2;
+    if (top <= d->N - 2) T2 += e2;
+  }
+  double E = (T - T1) / T;
+  if (d->N >= 2) {
+    double E2 = (T1 - T2) / T1;
+    if (E2 > E) E = E2;
+  }
+  return E;
+}
+
+/* Blending coefficient of one element before the neighbour smoothing. */
+static double alpha_raw(const or_desc *d, const double *ue) {
+  double E = or_indicator_energy(d, ue);
+  double T = 0.5 * pow(10.0, -1.8 * pow(d->N + 1.0, 0.25));
+  double s = log(9999.0);
+  double a = 1.0 / (1.0 + exp(-(s / T) * (E - T)));
+  if (a < 0.001) a = 0.0;
+  if (a > 0.999) a = 1.0;
+  if (a > d->alpha_max) a = d->alpha_max;
+  return a;
+}
+
+/* Exported: per element the coefficient before (raw, may be NULL) and after
+ * the smoothing a_e = max(raw_e, raw_nb / 2 over the 2 dim face neighbours);
+ * alpha_fixed >= 0 gives that value everywhere. */
+int or_blend_alpha(const or_desc *d, const double *U, double *raw, double *alpha) {
+  or_mesh m;
+  if (mesh_setup(d, &m) || d->eq != 0) return -1;
+  double *r = malloc(sizeof(double) * m.E);
+  double ue[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
+  for (int e = 0; e < m.E; ++e) {
+    if (d->alpha_fixed >= 0.0) { r[e] = d->alpha_fixed; continue; }
+    gather_elem(&m, U, e, ue);
+    r[e] = alpha_raw(d, ue);
+  }
+  for (int e = 0; e < m.E; ++e) {
+    double a = r[e];
+    if (d->alpha_fixed < 0.0)
+      for (int dir = 0; dir < d->dim; ++dir)
+        for (int off = -1; off <= 1; off += 2) {
+          double h = 0.5 * r[neighbour(d, e, dir, off)];
+          if (h > a) a = h;
+        }
+    if (raw) raw[e] = r[e];
+    alpha[e] = a;
+  }
+  free(r);
+  return 0;
+}
+
+/* First-order Rusanov flux of two states: (f(uL) + f(uR))/2 - lam/2 (uR - uL),
+ * lam = max(sigma(uL), sigma(uR)). */
+static void rusanov_flux(const or_desc *d, int dir, const double *uL, const double *uR, double *F) {
+  int M = nvars(d);
+  double fL[OR_MAXM], fR[OR_MAXM];
+  phys_flux(d, dir, uL, fL);
+  phys_flux(d, dir, uR, fR);
+  double lL = wave_speed(d, dir, uL), lR = wave_speed(d, dir, uR);
+  double lam = lL > lR ? lL : lR;
+  for (int v = 0; v < M; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+static void euler_rho_p(const or_desc *d, const double *u, double *rho, double *p) {
+  double v[3];
+  euler_prim(d, u, rho, v, p);
+}
+
+/* Largest theta in [0,1] with rho(u(theta)) >= rho(u(0))/10 and
+ * p(u(theta)) >= p(u(0))/10 along u(theta) = u0 + theta du (density linear in
+ * theta; pressure concave, so its chord bound is safe). 0 if u0 itself is not
+ * admissible. */
+static double admissible_theta(const or_desc *d, const double *u0, const double *du) {
+  int M = nvars(d);
+  double r0, p0;
+  euler_rho_p(d, u0, &r0, &p0);
+  if (!(r0 > 0.0) || !(p0 > 0.0)) return 0.0;
+  double u1[OR_MAXM];
+  for (int v = 0; v < M; ++v) u1[v] = u0[v] + du[v];
+  double r1, p1;
+  euler_rho_p(d, u1, &r1, &p1);
+  double theta = 1.0;
+  double er = 0.1 * r0;
+  if (r1 < er) theta = (r0 - er) / (r0 - r1);
+  double ut[OR_MAXM];
+  for (int v = 0; v < M; ++v) ut[v] = u0[v] + theta * du[v];
+  double rt, pt;
+  euler_rho_p(d, ut, &rt, &pt);
+  double ep = 0.1 * p0;
+  if (pt < ep) theta = theta * (p0 - ep) / (p0 - pt);
+  return theta;
+}
+
+/* The element-face flux of the limited step (readings above).  um, up: u^n
+ * traces of the '-' and '+' element; umi, upi: u^n at the neighbouring
+ * interior node of each (index N-1 of '-', 1 of '+'); Fho: time-averaged
+ * Rusanov flux; wN, w0: end subcell widths; a_f: face coefficient. */
+static void limited_face_flux(const or_desc *d, int dir, const double *um, const double *up, const double *umi,
+                              const double *upi, const double *Fho, double a_f, double dt, double dx, double wN,
+                              double w0, double *F) {
+  int M = nvars(d);
+  double flo[OR_MAXM], Fb[OR_MAXM];
+  rusanov_flux(d, dir, um, up, flo);
+  /* a_f = 1 takes f_lo alone (so a high-order flux that is not finite on
+   * data the first-order scheme still handles does not enter) */
+  for (int v = 0; v < M; ++v) Fb[v] = a_f >= 1.0 ? flo[v] : (1.0 - a_f) * Fho[v] + a_f * flo[v];
+  if (!(a_f > 0.0)) {
+    for (int v = 0; v < M; ++v) F[v] = Fb[v];
+    return;
+  }
+  /* one-direction low-order states of the two end subcells, with the face
+   * flux f_lo (theta = 0) and with the blend (theta = 1):
+   *   '-' end: u_N - (dim dt/(w_N dx)) (F - f_{N-1/2}),  '+' end: u_0 - (dim dt/(w_0 dx)) (f_{1/2} - F) */
+  double fmi[OR_MAXM], fpi[OR_MAXM];
+  rusanov_flux(d, dir, umi, um, fmi);
+  rusanov_flux(d, dir, up, upi, fpi);
+  double cm = d->dim * dt / (wN * dx), cp = d->dim * dt / (w0 * dx);
+  double lm[OR_MAXM], dm[OR_MAXM], lp[OR_MAXM], dpl[OR_MAXM];
+  for (int v = 0; v < M; ++v) {
+    lm[v] = um[v] - cm * (flo[v] - fmi[v]);
+    dm[v] = -cm * (Fb[v] - flo[v]);
+    lp[v] = up[v] - cp * (fpi[v] - flo[v]);
+    dpl[v] = cp * (Fb[v] - flo[v]);
+  }
+  double tm = admissible_theta(d, lm, dm), tp = admissible_theta(d, lp, dpl);
+  double theta = tm < tp ? tm : tp;
+  for (int v = 0; v < M; ++v) F[v] = flo[v] + theta * (Fb[v] - flo[v]);
+}
+
+/* Exported for pins: the limited element-face flux (arguments as above). */
+int or_limited_face_flux(const or_desc *d, int dir, const double *um, const double *up, const double *umi,
+                         const double *upi, const double *Fho, double a_f, double dt, double dx, double wN,
+                         double w0, double *F) {
+  if (d->eq != 0 || dir < 0 || dir >= d->dim) return -1;
+  limited_face_flux(d, dir, um, up, umi, upi, Fho, a_f, dt, dx, wN, w0, F);
+  return 0;
+}
+
 /* Time-averaged data of a set of elements: element e sits at local index
  * loc[e] of the W arrays (Fbar, Fnc: [dir][nloc][np][M]). */
 typedef struct {
@@ -638,11 +877,17 @@ static void set_stages(const or_desc *d, const or_mesh *m, const double *Un, dou
 /* 2. final update of element e ([node][var] into unew), with the face terms of
  *    eq. crkfr.non.cons.final evaluated at both faces of every direction; the
  *    element and its neighbours must be in the set. */
-static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int e, double dt, double *unew) {
+/*    alpha != NULL: the limited step (subcell blending, readings above): the
+ *    face fluxes of both updates are the limited face fluxes, and the result
+ *    is (1 - a_e) u^H + a_e u^L. */
+static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int e, double dt, double *unew,
+                       const double *alpha) {
   int M = m->M, np = m->np, dim = d->dim;
   size_t sz = (size_t)np * M;
   const or_work *W = &S->W;
   const int ke = S->loc[e];
+  /* limited step: face flux per direction, side and face node */
+  double *Fface = alpha ? malloc(sizeof(double) * 3 * 2 * np * M) : NULL;
   for (size_t k = 0; k < sz; ++k) unew[k] = W->un[ke * sz + k] - dt * W->Rbar[ke * sz + k];
   for (int dir = 0; dir < dim; ++dir) {
     for (int side = 0; side < 2; ++side) {
@@ -674,6 +919,23 @@ static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int 
         double lam = lm > lp ? lm : lp;
         double Fnum[OR_MAXM], ncs[OR_MAXM];
         for (int v = 0; v < M; ++v) Fnum[v] = 0.5 * (Fm[v] + Fp[v]) - 0.5 * lam * (Up[v] - Um[v]);
+        if (alpha) {
+          /* limited face flux from the '-' and '+' elements' u^n (traces and
+           * the neighbouring interior nodes) and their coefficients */
+          int emi = side ? e : nb, epl = side ? nb : e;
+          const double *unm = &W->un[(size_t)S->loc[emi] * sz], *unp = &W->un[(size_t)S->loc[epl] * sz];
+          int im[3] = {fijk[0], fijk[1], fijk[2]}, ip[3] = {fijk[0], fijk[1], fijk[2]};
+          im[dir] = d->N - 1;
+          ip[dir] = 1;
+          double a_f = 0.5 * (alpha[emi] + alpha[epl]);
+          double Fl[OR_MAXM];
+          limited_face_flux(d, dir, um, up, &unm[node_id(m, im, dim) * M], &unp[node_id(m, ip, dim) * M], Fnum, a_f,
+                            dt, m->dx[dir], m->w[d->N], m->w[0], Fl);
+          for (int v = 0; v < M; ++v) {
+            Fnum[v] = Fl[v];
+            Fface[((size_t)(dir * 2 + side) * np + fnode) * M + v] = Fl[v];
+          }
+        }
         /* F^{num,+-}_nc = B(u^{n,+-}) g^avg(U), or with ncflux 1 (eq. bad.numflux.non.cons)
          * sum_j b_j B(u^{(j),+-}) g^avg(u^(j)) from the stage traces of both sides;
          * then the jump F^num_{+-} - F^tot_{+-} */
@@ -707,24 +969,75 @@ static void set_update(const or_desc *d, const or_mesh *m, const or_set *S, int 
       }
     }
   }
+  if (alpha) {
+    /* low-order update: first-order finite volumes on the subcells of every
+     * line, the limited face fluxes at the element faces; then the blend */
+    const double *ue = &W->un[ke * sz];
+    double *ul = malloc(sizeof(double) * sz);
+    for (size_t k = 0; k < sz; ++k) ul[k] = ue[k];
+    for (int p = 0; p < np; ++p) {
+      int ijk[3];
+      node_ijk(m, p, dim, ijk);
+      for (int dir = 0; dir < dim; ++dir) {
+        int pd = ijk[dir];
+        int fi[3] = {ijk[0], ijk[1], ijk[2]};
+        fi[dir] = 0;
+        int fnode = node_id(m, fi, dim);
+        double fL[OR_MAXM], fR[OR_MAXM];
+        int q[3] = {ijk[0], ijk[1], ijk[2]};
+        if (pd == 0) {
+          for (int v = 0; v < M; ++v) fL[v] = Fface[((size_t)(dir * 2 + 0) * np + fnode) * M + v];
+        } else {
+          q[dir] = pd - 1;
+          rusanov_flux(d, dir, &ue[node_id(m, q, dim) * M], &ue[p * M], fL);
+        }
+        if (pd == d->N) {
+          for (int v = 0; v < M; ++v) fR[v] = Fface[((size_t)(dir * 2 + 1) * np + fnode) * M + v];
+        } else {
+          q[dir] = pd + 1;
+          rusanov_flux(d, dir, &ue[p * M], &ue[node_id(m, q, dim) * M], fR);
+        }
+        for (int v = 0; v < M; ++v) ul[p * M + v] -= dt * (fR[v] - fL[v]) / (m->w[pd] * m->dx[dir]);
+      }
+    }
+    /* a_e = 1 takes u^L alone (u^H may not be finite where the
+     * first-order update still is) */
+    double a = alpha[e];
+    for (size_t k = 0; k < sz; ++k) unew[k] = a >= 1.0 ? ul[k] : (1.0 - a) * unew[k] + a * ul[k];
+    free(ul);
+    free(Fface);
+  }
+}
+
+/* validity of the limiter options: Euler, reduced non-conservative flux,
+ * 0 <= alpha_max <= 1 */
+static int limiter_ok(const or_desc *d) {
+  if (!d->limiter) return 1;
+  return d->eq == 0 && d->ncflux == 0 && d->alpha_max >= 0.0 && d->alpha_max <= 1.0 && d->alpha_fixed <= 1.0;
 }
 
 /* Exported: one cRKFR step u^n -> u^{n+1} with the given dt. */
 int or_step(const or_desc *d, const double *Un, double dt, double *Unew) {
   or_mesh m;
-  if (mesh_setup(d, &m)) return -1;
+  if (mesh_setup(d, &m) || !limiter_ok(d)) return -1;
   int M = m.M, np = m.np, E = m.E;
   size_t sz = (size_t)np * M;
+  double *alpha = NULL;
+  if (d->limiter) {
+    alpha = malloc(sizeof(double) * E);
+    or_blend_alpha(d, Un, NULL, alpha);
+  }
   or_set S;
   set_alloc(&S, E, E, sz, d->dim, d->ncflux == 1 ? m.S : 0);
   for (int e = 0; e < E; ++e) set_stages(d, &m, Un, dt, &S, e, e);
   for (int e = 0; e < E; ++e) {
     double unew[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
-    set_update(d, &m, &S, e, dt, unew);
+    set_update(d, &m, &S, e, dt, unew, alpha);
     for (int v = 0; v < M; ++v)
       for (int p = 0; p < np; ++p) Unew[((size_t)v * E + e) * np + p] = unew[p * M + v];
   }
   set_free(&S);
+  free(alpha);
   return 0;
 }
 
@@ -734,11 +1047,16 @@ int or_step(const or_desc *d, const double *Un, double dt, double *Unew) {
  * [var][k][node] for sel[k]. */
 int or_step_elements(const or_desc *d, const double *Un, double dt, int nsel, const int *sel, double *Unew_sel) {
   or_mesh m;
-  if (mesh_setup(d, &m)) return -1;
+  if (mesh_setup(d, &m) || !limiter_ok(d)) return -1;
   int M = m.M, np = m.np, E = m.E, dim = d->dim;
   size_t sz = (size_t)np * M;
   for (int k = 0; k < nsel; ++k)
     if (sel[k] < 0 || sel[k] >= E) return -1;
+  double *alpha = NULL;
+  if (d->limiter) {
+    alpha = malloc(sizeof(double) * E);
+    or_blend_alpha(d, Un, NULL, alpha);
+  }
   or_set S;
   set_alloc(&S, E, nsel * (1 + 2 * dim), sz, dim, d->ncflux == 1 ? m.S : 0);
   int nloc = 0;
@@ -755,11 +1073,12 @@ int or_step_elements(const or_desc *d, const double *Un, double dt, int nsel, co
   }
   for (int k = 0; k < nsel; ++k) {
     double unew[OR_MAXNP * OR_MAXNP * OR_MAXNP * OR_MAXM];
-    set_update(d, &m, &S, sel[k], dt, unew);
+    set_update(d, &m, &S, sel[k], dt, unew, alpha);
     for (int v = 0; v < M; ++v)
       for (int p = 0; p < np; ++p) Unew_sel[((size_t)v * nsel + k) * np + p] = unew[p * M + v];
   }
   set_free(&S);
+  free(alpha);
   return 0;
 }
 
@@ -846,7 +1165,7 @@ int or_fr_rhs(const or_desc *d, const double *Un, double *RHS) {
 /* ------------------------------------------------------------------------- */
 int or_rkfr_step(const or_desc *d, const double *Un, double dt, double *Unew) {
   or_mesh m;
-  if (d->surf != 0 || mesh_setup(d, &m)) return -1;
+  if (d->surf != 0 || d->limiter || mesh_setup(d, &m)) return -1;
   size_t tot = (size_t)m.M * m.E * m.np;
   double *K = malloc(sizeof(double) * tot * m.S);
   double *us = malloc(sizeof(double) * tot);

@@ -42,7 +42,8 @@ class Desc(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
                 ("vol", ctypes.c_int), ("surf", ctypes.c_int), ("ncflux", ctypes.c_int),
                 ("tab_s", ctypes.c_int), ("tab_A", ctypes.POINTER(ctypes.c_double)),
-                ("tab_b", ctypes.POINTER(ctypes.c_double))]
+                ("tab_b", ctypes.POINTER(ctypes.c_double)), ("limiter", ctypes.c_int),
+                ("alpha_max", ctypes.c_double), ("alpha_fixed", ctypes.c_double)]
 
 
 _lib = None
@@ -75,6 +76,10 @@ def lib():
         _lib.or_fr_rhs.argtypes = [P, D, D]
         _lib.or_rkfr_step.argtypes = [P, D, ctypes.c_double, D]
         _lib.or_totals.argtypes = [P, D, D]
+        _lib.or_blend_alpha.argtypes = [P, D, D, D]
+        _lib.or_indicator_energy.argtypes = [P, D]
+        _lib.or_indicator_energy.restype = ctypes.c_double
+        _lib.or_limited_face_flux.argtypes = [P, ctypes.c_int, D, D, D, D, D] + [ctypes.c_double] * 5 + [D]
     return _lib
 
 
@@ -88,7 +93,8 @@ def make_desc(mesh):
     paper_2604_02125_gb300.inputs: eq, dim, N, cells, lo, hi, gamma, cfl,
     c_h, vol, surf; optional: ncflux 'reduced' | 'stages' (the non-conservative
     numerical flux of the cRKFR step), tableau (A, b): an explicit RK tableau
-    of s <= 7 stages in place of the degree's)."""
+    of s <= 7 stages in place of the degree's, limiter (bool: subcell blending),
+    alpha_max, alpha_fixed (a blending coefficient forced in every element))."""
     d = Desc()
     d.eq = EQ[mesh.get("eq", "euler")]
     d.dim = mesh["dim"]
@@ -106,6 +112,10 @@ def make_desc(mesh):
     d.vol = VOL[mesh.get("vol", "ec")]
     d.surf = SURF[mesh.get("surf", "rusanov")]
     d.ncflux = NCFLUX[mesh.get("ncflux", "reduced")]
+    d.limiter = 1 if mesh.get("limiter") else 0
+    d.alpha_max = float(mesh.get("alpha_max", 1.0))
+    af = mesh.get("alpha_fixed")
+    d.alpha_fixed = -1.0 if af is None else float(af)
     if mesh.get("tableau") is not None:
         A, b = mesh["tableau"]
         s = len(b)
@@ -281,3 +291,33 @@ def totals(mesh, U):
     out = np.zeros(nvars(mesh) + 2)
     lib().or_totals(ctypes.byref(d), _ptr(U), _ptr(out))
     return out
+
+
+def blend_alpha(mesh, U):
+    """(raw, smoothed) blending coefficient per element of the subcell
+    blending limiter (Euler)."""
+    d = make_desc(mesh)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    E = U.shape[1]
+    raw, a = np.zeros(E), np.zeros(E)
+    if lib().or_blend_alpha(ctypes.byref(d), _ptr(U), _ptr(raw), _ptr(a)):
+        raise ValueError("oracle rejected the mesh descriptor")
+    return raw, a
+
+
+def indicator_energy(mesh, ue):
+    """Highest-mode energy fraction of rho p of one element; ue is [node][var]."""
+    d = make_desc(mesh)
+    ue = np.ascontiguousarray(ue, dtype=np.float64)
+    return lib().or_indicator_energy(ctypes.byref(d), _ptr(ue))
+
+
+def limited_face_flux(mesh, direction, um, up, umi, upi, Fho, a_f, dt, dx, wN, w0):
+    """The limited element-face flux of the subcell blending limiter."""
+    d = make_desc(mesh)
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (um, up, umi, upi, Fho)]
+    F = np.zeros(nvars(mesh))
+    if lib().or_limited_face_flux(ctypes.byref(d), direction, *[_ptr(a) for a in arrs], float(a_f), float(dt),
+                                  float(dx), float(wN), float(w0), _ptr(F)):
+        raise ValueError("oracle rejected the arguments")
+    return F
