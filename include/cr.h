@@ -71,6 +71,13 @@ extern "C" {
                                   the face traces of every stage are exchanged (seven values per
                                   stage and face node); GLM-MHD with CR_SCHEME_CRKFR only        */
 
+/* subcell blending limiter (the paper's Sec. 4 runs: the cRKFR update blended
+ * per element with a first-order subcell finite-volume update, coefficient
+ * from a modal smoothness indicator capped by alpha_max; compressible Euler
+ * with CR_SCHEME_CRKFR and the single-solve form only) */
+#define CR_LIMITER_NONE     0
+#define CR_LIMITER_BLENDING 1
+
 /* arithmetic of the element-local work */
 #define CR_FP64          0     /* every step of the path in FP64                        */
 #define CR_FP32_PAIRFLUX 1     /* stages, pair fluxes, time averages and face fluxes in
@@ -94,6 +101,13 @@ typedef struct {
                         cr_step_noalloc take CR_SCHEME_CRKFR only                        */
   int ncflux;        /* CR_NCFLUX_REDUCED (0) | CR_NCFLUX_STAGES; the batched form and
                         cr_step_noalloc take CR_NCFLUX_REDUCED only                      */
+  int limiter;       /* CR_LIMITER_NONE (0) | CR_LIMITER_BLENDING: per element
+                        u^{n+1} = (1 - a) u^H + a u^L, u^H the cRKFR update, u^L first-
+                        order finite volumes on the subcells of the GLL points (widths
+                        w_p dx), both with one blended, admissibility-corrected flux per
+                        element-face node; a from the highest-mode energy of rho p;
+                        CR_EULER, CR_SCHEME_CRKFR, single solve only                      */
+  double alpha_max;  /* cap of the blending coefficient, 0..1 (limiter only)             */
 } cr_mesh_desc;
 
 typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
@@ -114,7 +128,10 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  *   cuda_stream: cudaStream_t on which all work is enqueued (NULL = legacy default).
  * The library allocates and owns all device buffers (state, stage/trace
  * scratch, step records; CR_SCHEME_RKFR adds a stage state and s - 1 stage
- * increments, CR_NCFLUX_STAGES the stage traces after the face records).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+ * increments, CR_NCFLUX_STAGES the stage traces after the face records,
+ * CR_LIMITER_BLENDING a second state buffer -- the limited step reads u^n
+ * from one and writes u^{n+1} to the other -- and one coefficient per
+ * element).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
 /* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */
@@ -205,7 +222,8 @@ int cr_check_conversions(long long n, unsigned long long seed, long long *mismat
  *   dt_out     : device pointer receiving the dt used (FP64), or NULL.
  *   cuda_stream: stream for all work (asynchronous; nothing is synchronised).
  * dt follows the descriptor (CFL rule on u^n, or dt_fixed); desc->scheme must
- * be CR_SCHEME_CRKFR and desc->ncflux CR_NCFLUX_REDUCED (CR_EINVAL otherwise).  The scratch
+ * be CR_SCHEME_CRKFR, desc->ncflux CR_NCFLUX_REDUCED and desc->limiter
+ * CR_LIMITER_NONE (CR_EINVAL otherwise).  The scratch
  * (residual sums, face traces, reductions, step record) lives in one static
  * device array of CR_NOALLOC_SCRATCH_BYTES per device, held until the
  * process exits; a mesh needing more returns CR_ETOOLARGE (roughly 80k nodes

@@ -34,7 +34,8 @@ class MeshDesc(ctypes.Structure):
                 ("cells", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("c_h", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("vol", ctypes.c_int), ("surf", ctypes.c_int),
-                ("prec", ctypes.c_int), ("scheme", ctypes.c_int), ("ncflux", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("scheme", ctypes.c_int), ("ncflux", ctypes.c_int),
+                ("limiter", ctypes.c_int), ("alpha_max", ctypes.c_double)]
 
 
 _lib = None
@@ -90,7 +91,8 @@ def make_desc(mesh, prec="fp64", dt_fixed=0.0, scheme=None):
     """Descriptor of a mesh dict; scheme ('crkfr' or 'rkfr', the multi-stage
     scheme) defaults to the dict's 'scheme' key, else 'crkfr'; the dict's
     'ncflux' key ('reduced' or 'stages', GLM-MHD) selects the non-conservative
-    numerical flux."""
+    numerical flux; 'limiter' (bool) and 'alpha_max' the subcell blending
+    limiter (Euler)."""
     d = MeshDesc()
     d.eq = EQ[mesh.get("eq", "euler")]
     d.dim = mesh["dim"]
@@ -109,6 +111,8 @@ def make_desc(mesh, prec="fp64", dt_fixed=0.0, scheme=None):
     d.prec = PREC[prec]
     d.scheme = SCHEME[scheme or mesh.get("scheme", "crkfr")]
     d.ncflux = NCFLUX[mesh.get("ncflux", "reduced")]
+    d.limiter = 1 if mesh.get("limiter") else 0
+    d.alpha_max = float(mesh.get("alpha_max", 1.0))
     return d
 
 

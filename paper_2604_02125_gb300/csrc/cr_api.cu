@@ -155,6 +155,40 @@ void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
   }
 }
 
+// Limiter tables.  Modal coefficients of the orthonormal Legendre basis
+// phi_j = sqrt((2j+1)/2) P_j on [-1,1] from GLL node values: GLL quadrature is
+// exact to degree 2N-1, so the discrete Gram matrix sum_p W_p phi_i phi_j is
+// diagonal, with 1 for j < N and (2N+1)/N for j = N (the discrete norm of P_N
+// is 2/N against 2/(2N+1)); hence m_j = sum_p W_p phi_j(x_p) v_p / G_jj,
+// W_p = 2 w_p the weights on [-1,1].
+void fill_lim_tab(int N, double alpha_max, LimTab* lt) {
+  std::memset(lt, 0, sizeof(*lt));
+  double xi[6], w[6], D[6][6];
+  ref_tables(N, xi, w, D);
+  for (int p = 0; p <= N; ++p) {
+    const double x = 2.0 * xi[p] - 1.0;
+    double pm1 = 1.0, pk = x;   // P_0, P_1
+    for (int j = 0; j <= N; ++j) {
+      double Pj;
+      if (j == 0) Pj = 1.0;
+      else if (j == 1) Pj = x;
+      else {
+        const double pn = ((2.0 * j - 1.0) * x * pk - (j - 1.0) * pm1) / j;
+        pm1 = pk;
+        pk = pn;
+        Pj = pn;
+      }
+      const double phi = std::sqrt((2.0 * j + 1.0) / 2.0) * Pj;
+      const double g = j < N ? 1.0 : (2.0 * N + 1.0) / N;
+      lt->vinv[j][p] = 2.0 * w[p] * phi / g;
+    }
+    lt->w01[p] = w[p];
+  }
+  lt->tau = 0.5 * std::pow(10.0, -1.8 * std::pow(N + 1.0, 0.25));
+  lt->sharp = std::log(9999.0);
+  lt->alpha_max = alpha_max;
+}
+
 void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* plc) {
   LaunchCtx& lc = *plc;
   std::memset(&lc, 0, sizeof(lc));
@@ -216,6 +250,10 @@ struct cr_ctx {
   size_t totals_blocks = 0;
   bool has_state = false;
   int parity = 0;     // slot of the CFL reduction of the current state
+  // state buffers: ubuf[0] only, or with the limiter two, the state of parity p
+  // in ubuf[p] (the limited step reads one and writes the other)
+  double* ubuf[2] = {nullptr, nullptr};
+  bool limited = false;
   cudaStream_t cap_stream = nullptr;
   // graphs of 1 and 16 steps, one per starting parity
   cudaGraphExec_t g1[2] = {nullptr, nullptr}, g16[2] = {nullptr, nullptr};
@@ -259,6 +297,11 @@ static bool desc_valid(const cr_mesh_desc& d) {
     if (d.cells[k] < 1) return false;
     if (!(d.hi[k] > d.lo[k])) return false;
   }
+  // the subcell blending limiter: Euler, single-stage scheme, 0 <= alpha_max <= 1
+  if (d.limiter != CR_LIMITER_NONE &&
+      (d.limiter != CR_LIMITER_BLENDING || d.eq != CR_EULER || d.scheme != CR_SCHEME_CRKFR ||
+       !(d.alpha_max >= 0.0 && d.alpha_max <= 1.0)))
+    return false;
   return true;
 }
 
@@ -269,7 +312,11 @@ static void free_single(cr_ctx* c) {
     c->g1[p] = c->g16[p] = nullptr;
   }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  cudaFree(c->lc.u);
+  cudaFree(c->ubuf[0]);
+  cudaFree(c->ubuf[1]);
+  c->ubuf[0] = c->ubuf[1] = nullptr;
+  c->lc.u = nullptr;
+  cudaFree(c->lc.araw);
   cudaFree(c->lc.rbar);
   cudaFree(c->lc.trace);
   cudaFree(c->lc.st);
@@ -280,8 +327,22 @@ static void free_single(cr_ctx* c) {
 }
 
 // one step from the state whose CFL reduction sits in slot `parity`
+// state buffer of the given parity (the only one without the limiter)
+static double* state_buf(const cr_ctx* c, int parity) { return c->ubuf[c->limited ? (parity & 1) : 0]; }
+
 static int launch_step(cr_ctx* c, cudaStream_t s, int parity) {
   c->lc.slot = parity;
+  if (c->limited) {
+    // coefficients of u^n, the cRKFR volume work, then the limited face /
+    // update kernel from the parity's buffer into the other one
+    c->lc.u = state_buf(c, parity);
+    c->lc.u_next = state_buf(c, parity ^ 1);
+    CR_TRY(c->ops.alpha(c->lc, s));
+    CR_TRY(c->ops.volume(c->lc, s));
+    CR_TRY(c->ops.face_limited(c->lc, s));
+    c->lc.u = state_buf(c, c->parity);
+    return CR_OK;
+  }
   if (c->desc[0].scheme == CR_SCHEME_RKFR) {
     // stage j: volume part on u^(j) (u^n for j = 0), face / update part
     // forming u^(j+1) (the state itself after the last stage)
@@ -331,7 +392,15 @@ static int init_single(cr_ctx* c) {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) rc = cuda_status(e);
   };
-  al((void**)&lc.u, sizeof(double) * (size_t)o.M * nodes);
+  c->limited = d.limiter == CR_LIMITER_BLENDING;
+  if (c->limited && (!o.alpha || !o.face_limited)) return CR_EINVAL;
+  al((void**)&c->ubuf[0], sizeof(double) * (size_t)o.M * nodes);
+  if (c->limited) {
+    al((void**)&c->ubuf[1], sizeof(double) * (size_t)o.M * nodes);
+    al((void**)&lc.araw, sizeof(double) * (size_t)E);
+    fill_lim_tab(d.degree_N, d.alpha_max, &lc.lt);
+  }
+  lc.u = c->ubuf[0];
   al(&lc.rbar, o.real_bytes * (size_t)o.M * nodes);
   al(&lc.trace, o.real_bytes * ((size_t)o.dim * 2 * o.C * NFt + o.ncs_per_elem * (size_t)E));
   al((void**)&lc.st, sizeof(DevState));
@@ -408,6 +477,7 @@ int cr_set_state(cr_ctx* c, int solve, const double* u, int u_on_device) {
   if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
   if (c->batched) return batched_set_state(c->batched, solve, u, u_on_device);
   const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  c->lc.u = state_buf(c, 0);
   CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->stream));
   CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
@@ -423,6 +493,7 @@ int cr_set_state_async(cr_ctx* c, int solve, const double* u, int u_on_device) {
   if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
   if (c->batched) return batched_set_state_async(c->batched, solve, u, u_on_device);
   const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
+  c->lc.u = state_buf(c, 0);
   CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->stream));
   CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
@@ -437,8 +508,8 @@ int cr_get_state_async(cr_ctx* c, int solve, double* u, int u_on_device) {
   if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
   if (c->batched) return batched_get_state_async(c->batched, solve, u, u_on_device);
   const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
-  CR_TRY(cudaMemcpyAsync(u, c->lc.u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                         c->stream));
+  CR_TRY(cudaMemcpyAsync(u, state_buf(c, c->parity), bytes,
+                         u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   return CR_OK;
 }
 
@@ -451,6 +522,7 @@ int cr_step(cr_ctx* c, int nsteps) {
   for (; k < nsteps; ++k) {
     CR_TRY(cudaGraphLaunch(c->g1[c->parity], c->stream));
     c->parity ^= 1;
+    c->lc.u = state_buf(c, c->parity);
   }
   return CR_OK;
 }
@@ -465,8 +537,8 @@ int cr_get_state(cr_ctx* c, int solve, double* u, int u_on_device) {
   if (!c || !u || solve < 0 || solve >= c->n_solves) return CR_EINVAL;
   if (c->batched) return batched_get_state(c->batched, solve, u, u_on_device);
   const size_t bytes = sizeof(double) * (size_t)c->M * c->E * c->NP;
-  CR_TRY(cudaMemcpyAsync(u, c->lc.u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                         c->stream));
+  CR_TRY(cudaMemcpyAsync(u, state_buf(c, c->parity), bytes,
+                         u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   return read_status(c);
 }
 
@@ -514,21 +586,28 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
       break;
     }
     c->lc.slot = c->parity;
+    c->lc.u = state_buf(c, c->parity);
+    c->lc.u_next = state_buf(c, c->parity ^ 1);
     for (int j = 0; j < S && rc == CR_OK; ++j) {
       cudaEvent_t* e4 = &ev[4 * ((size_t)k * S + j)];
       cudaEventRecord(e4[0], c->stream);
-      cudaError_t e = rk ? c->ops.volume_stage(c->lc, c->stream, j == 0 ? c->lc.u : c->lc.ustage, j == 0)
-                         : c->ops.volume(c->lc, c->stream);
+      // limiter: the coefficient kernel counts with the volume kernel
+      cudaError_t e = c->limited ? c->ops.alpha(c->lc, c->stream) : cudaSuccess;
+      if (e == cudaSuccess)
+        e = rk ? c->ops.volume_stage(c->lc, c->stream, j == 0 ? c->lc.u : c->lc.ustage, j == 0)
+               : c->ops.volume(c->lc, c->stream);
       if (e != cudaSuccess) rc = CR_ECUDA;
       cudaEventRecord(e4[1], c->stream);
       cudaEventRecord(e4[2], c->stream);
       if (rc == CR_OK) {
-        e = rk ? c->ops.face_stage(c->lc, c->stream, j, S) : c->ops.face_update(c->lc, c->stream);
+        e = rk ? c->ops.face_stage(c->lc, c->stream, j, S)
+               : (c->limited ? c->ops.face_limited(c->lc, c->stream) : c->ops.face_update(c->lc, c->stream));
         if (e != cudaSuccess) rc = CR_ECUDA;
       }
       cudaEventRecord(e4[3], c->stream);
     }
     if (rc == CR_OK) c->parity ^= 1;
+    c->lc.u = state_buf(c, c->parity);
   }
   if (rc == CR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CR_ECUDA;
   double tv = 0.0, tf = 0.0;
@@ -567,7 +646,8 @@ int cr_tuning_info(cr_ctx* c, char* buf, size_t len) {
     std::snprintf(tmp, sizeof(tmp),
                   "{\"scheme\": \"%s\", \"volume\": \"%s\", \"elements_per_cta\": %d, \"face\": \"%s\"}",
                   c->desc[0].scheme == CR_SCHEME_RKFR ? "rkfr" : "crkfr", c->ops.lanes ? "lanes" : "tile",
-                  c->ops.lanes ? 32 : c->lc.epb, c->ops.threads_face > 0 ? "lanes" : "per-node");
+                  c->ops.lanes ? 32 : c->lc.epb,
+                  c->limited ? "limited per-node" : (c->ops.threads_face > 0 ? "lanes" : "per-node"));
     info = tmp;
   }
   std::snprintf(buf, len, "%s", info.c_str());

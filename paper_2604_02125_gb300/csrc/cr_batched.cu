@@ -96,7 +96,9 @@ int batched_init(BatchedCtx** out, const cr_mesh_desc* desc, int n, cudaStream_t
   // all solves take the single-stage scheme and share the system, dimension,
   // precision and volume flux
   for (int k = 0; k < n; ++k)
-    if (desc[k].scheme != CR_SCHEME_CRKFR || desc[k].ncflux != CR_NCFLUX_REDUCED) return CR_EINVAL;
+    if (desc[k].scheme != CR_SCHEME_CRKFR || desc[k].ncflux != CR_NCFLUX_REDUCED ||
+        desc[k].limiter != CR_LIMITER_NONE)
+      return CR_EINVAL;
   for (int k = 1; k < n; ++k)
     if (desc[k].eq != desc[0].eq || desc[k].dim != desc[0].dim || desc[k].prec != desc[0].prec ||
         desc[k].vol != desc[0].vol)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include "../../include/cr.h"
+#include "crkfr_limiter.cuh"
 #include "crkfr_volume_lanes.cuh"
 
 namespace crk {
@@ -26,6 +27,11 @@ struct LaunchCtx {
   // increments K_0..K_{s-2} ([stage][var][elem][node], R)
   double* ustage;
   void* kbuf;
+  // subcell blending limiter: the state buffer the step writes (u holds u^n),
+  // the coefficients before smoothing (one per element) and the tables
+  double* u_next;
+  double* araw;
+  LimTab lt;
 };
 
 // One launch of a batched persistent kernel (all solves of one degree).
@@ -56,6 +62,10 @@ struct VariantOps {
   // stage j of s (intermediate stage states go to ustage, the last to u)
   cudaError_t (*volume_stage)(const LaunchCtx&, cudaStream_t, const double* u_in, int first);
   cudaError_t (*face_stage)(const LaunchCtx&, cudaStream_t, int j, int s);
+  // subcell blending limiter (Euler; null elsewhere): coefficients of u, then
+  // the limited face / update kernel from u into u_next
+  cudaError_t (*alpha)(const LaunchCtx&, cudaStream_t);
+  cudaError_t (*face_limited)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*lambda)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*totals)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*set_smem)(size_t bytes);
@@ -105,6 +115,10 @@ void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32);
 // ncflux = CR_NCFLUX_STAGES selects the GLM-MHD kernels with the stage-wise
 // non-conservative flux
 bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o, int ncflux = 0);
+
+// limiter tables of degree N (orthonormal Legendre modes from GLL values,
+// subcell widths, logistic threshold and sharpness)
+void fill_lim_tab(int N, double alpha_max, LimTab* lt);
 
 // elements per CTA of the volume kernel used by every context of a variant
 int default_epb(const VariantOps& o);

@@ -66,7 +66,7 @@ bool desc_ok(const cr_mesh_desc& d) {
   if (d.eq == CR_GLM_MHD && (d.dim != 2 || d.vol == CR_VOL_KEP)) return false;
   if (d.vol < 0 || d.vol > 2 || d.surf != CR_SURF_RUSANOV) return false;
   if (d.prec != CR_FP64 && d.prec != CR_FP32_PAIRFLUX) return false;
-  if (d.scheme != CR_SCHEME_CRKFR || d.ncflux != CR_NCFLUX_REDUCED) return false;
+  if (d.scheme != CR_SCHEME_CRKFR || d.ncflux != CR_NCFLUX_REDUCED || d.limiter != CR_LIMITER_NONE) return false;
   if (!(d.gamma > 1.0) || !(d.cfl > 0.0) || !(d.dt_fixed >= 0.0) || !(d.c_h >= 0.0)) return false;   // NaN fails
   for (int k = 0; k < d.dim; ++k)
     if (d.cells[k] < 1 || !(d.hi[k] > d.lo[k])) return false;

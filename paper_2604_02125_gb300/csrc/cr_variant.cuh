@@ -120,6 +120,24 @@ struct Variant {
     }
     return cudaGetLastError();
   }
+  static cudaError_t alpha(const LaunchCtx& c, cudaStream_t s) {
+    if constexpr (!EQ::NC) {
+      const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
+      k_alpha_raw<EQ, N><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
+  static cudaError_t face_limited(const LaunchCtx& c, cudaStream_t s) {
+    if constexpr (!EQ::NC) {
+      const long long total = c.ma.E * L::NP;
+      const unsigned grid = (unsigned)((total + 255) / 256);
+      k_face_update_limited<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.araw,
+                                                           c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt, c.slot);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
   static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {
     const long long total = c.ma.E * L::NP;
     const unsigned grid = (unsigned)((total + 255) / 256);
@@ -221,6 +239,8 @@ struct Variant {
     o->volume_stage = &volume_stage;
     o->face_stage = &face_stage;
     o->lambda = &lambda;
+    o->alpha = EQ::NC ? nullptr : &alpha;
+    o->face_limited = EQ::NC ? nullptr : &face_limited;
     o->totals = &totals;
     o->set_smem = &set_smem;
   }

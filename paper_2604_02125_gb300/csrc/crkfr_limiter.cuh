@@ -1,0 +1,334 @@
+// crkfr_limiter.cuh -- the subcell blending limiter of the cRKFR step (the
+// paper's Sec. 4 runs blend the update with a first-order subcell finite-volume
+// update, the blending coefficient capped by alpha_max; compressible Euler).
+//
+//  k_alpha_raw           per element, FP64: the modal smoothness indicator of
+//                        rho p (energy fraction of the highest orthonormal
+//                        Legendre modes), the logistic map, its clips and the
+//                        cap alpha_max.  One thread per element.
+//  k_face_update_limited per node: the cRKFR update u^H with the limited face
+//                        flux at element faces, the first-order subcell update
+//                        u^L with the same face flux, the blend
+//                        (1 - a_e) u^H + a_e u^L into the other state buffer,
+//                        and the CFL reduction of the result.
+//
+// The limited face flux at a face node between elements '-' and '+':
+//   F_blend = (1 - a_f) F^num + a_f f_lo   (f_lo alone where a_f = 1),
+//   a_f = (a_- + a_+)/2, F^num the time-averaged Rusanov flux of eq.
+//   numflux.cons (records of the volume kernel), f_lo the Rusanov flux of the
+//   two u^n traces; where a_f > 0, F = f_lo + theta (F_blend - f_lo) with the
+//   largest theta in [0,1] that keeps rho and p of both adjacent end
+//   subcells' one-direction low-order states at or above a tenth of their
+//   values with f_lo.  Both elements evaluate it from the same '-'/'+' data
+//   in the same order, so they get the same bits and the step conserves.
+// The smoothed coefficient a_e = max(raw_e, raw_nb / 2 over the face
+// neighbours) is formed where it is used, from k_alpha_raw's values.
+//
+// u^n is read from one state buffer and u^{n+1} written to the other (the
+// first-order fluxes read neighbouring nodes of other elements), so a limited
+// context ping-pongs between two buffers.
+#pragma once
+#include "crkfr_kernels.cuh"
+
+namespace crk {
+
+// Host-filled tables of the limiter (FP64).
+struct LimTab {
+  double vinv[6][6];   // orthonormal Legendre modes from GLL node values: m_j = sum_p vinv[j][p] v_p
+  double w01[6];       // GLL weights on [0,1] (subcell widths / dx)
+  double tau, sharp;   // logistic threshold 0.5 10^(-1.8 (N+1)^(1/4)) and sharpness ln 9999
+  double alpha_max;
+};
+
+// ---------------------------------------------------------------------------
+// Blending coefficient per element before smoothing
+// ---------------------------------------------------------------------------
+template <class EQ, int N>
+__global__ void __launch_bounds__(128)
+k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshArgs ma, const LimTab lt) {
+  constexpr int DIM = EQ::DIM, n = N + 1, NP = ipow(n, DIM);
+  const long long E = ma.E;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double m[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const double rho = u[(size_t)e * NP + p];
+    double mm = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const double mk = u[((size_t)(1 + k) * E + e) * NP + p];
+      mm += mk * mk;
+    }
+    const double Et = u[((size_t)(DIM + 1) * E + e) * NP + p];
+    // rho p = (gamma - 1)(rho E - |m|^2 / 2)
+    m[p] = (ma.gamma - 1.0) * (rho * Et - 0.5 * mm);
+  }
+  // modal coefficients: the 1D transform along every direction in turn
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int stride = ipow(n, d);
+#pragma unroll 1
+    for (int l = 0; l < NP / n; ++l) {
+      const int base = line_base<n>(l, stride);
+      double t[n];
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) acc += lt.vinv[j][p] * m[base + p * stride];
+        t[j] = acc;
+      }
+#pragma unroll
+      for (int j = 0; j < n; ++j) m[base + j * stride] = t[j];
+    }
+  }
+  // energy of all modes, of those of degree <= N-1 and <= N-2 in every direction
+  double T = 0.0, T1 = 0.0, T2 = 0.0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    int rem = p, top = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int j = rem % n;
+      rem /= n;
+      top = j > top ? j : top;
+    }
+    const double e2 = m[p] * m[p];
+    T += e2;
+    if (top <= N - 1) T1 += e2;
+    if (top <= N - 2) T2 += e2;
+  }
+  double En = (T - T1) / T;
+  if (N >= 2) En = fmax(En, (T1 - T2) / T1);
+  double a = 1.0 / (1.0 + exp(-(lt.sharp / lt.tau) * (En - lt.tau)));
+  if (a < 0.001) a = 0.0;
+  if (a > 0.999) a = 1.0;
+  araw[e] = fmin(a, lt.alpha_max);
+}
+
+// smoothed coefficient of element e: max(raw_e, raw_nb / 2 over the face neighbours)
+template <int DIM>
+__device__ __forceinline__ double alpha_smoothed(const double* __restrict__ araw, unsigned e, const MeshArgs& ma) {
+  unsigned c[3] = {0, 0, 0};
+  elem_coords<DIM>(e, ma, c);
+  double a = araw[e];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    a = fmax(a, 0.5 * araw[neighbour_of(e, c, d, +1, ma)]);
+    a = fmax(a, 0.5 * araw[neighbour_of(e, c, d, -1, ma)]);
+  }
+  return a;
+}
+
+// u^n of node p of element e in the path's arithmetic
+template <int M, typename R>
+__device__ __forceinline__ void load_node(const double* __restrict__ u, long long E, unsigned e, int NP, int p, R* out) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    const double x = u[((size_t)v * E + e) * NP + p];
+    if constexpr (sizeof(R) == 4) out[v] = d2f_int(x);
+    else out[v] = x;
+  }
+}
+
+// first-order Rusanov flux in direction d: (f(a) + f(b))/2 - lam/2 (b - a)
+template <class EQ, typename R>
+__device__ __forceinline__ void rusanov_lo(int d, const R* a, const R* b, R* F, const PhysParams<R>& pp) {
+  constexpr int M = EQ::M;
+  R qa[EQ::P], qb[EQ::P], fa[M], fb[M];
+  EQ::pair_data(a, qa, pp);
+  EQ::pair_data(b, qb, pp);
+  EQ::flux(d, qa, fa, pp);
+  EQ::flux(d, qb, fb, pp);
+  const R lam = fmax(EQ::wave_speed(d, qa, pp), EQ::wave_speed(d, qb, pp));
+#pragma unroll
+  for (int v = 0; v < M; ++v) F[v] = R(0.5) * (fa[v] + fb[v]) - R(0.5) * lam * (b[v] - a[v]);
+}
+
+template <class EQ, typename R>
+__device__ __forceinline__ void rho_p_of(const R* u, R& rho, R& p, const PhysParams<R>& pp) {
+  constexpr int DIM = EQ::DIM;
+  rho = u[0];
+  R mm = R(0);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) mm += u[1 + k] * u[1 + k];
+  p = (pp.gamma - R(1)) * (u[DIM + 1] - R(0.5) * mm / rho);
+}
+
+// Largest theta in [0,1] keeping rho and p of u0 + theta du at or above a
+// tenth of those of u0 (0 if u0 is not admissible).
+template <class EQ, typename R>
+__device__ __forceinline__ R admissible_theta(const R* u0, const R* du, const PhysParams<R>& pp) {
+  constexpr int M = EQ::M;
+  R r0, p0;
+  rho_p_of<EQ, R>(u0, r0, p0, pp);
+  if (!(r0 > R(0)) || !(p0 > R(0))) return R(0);
+  R u1[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) u1[v] = u0[v] + du[v];
+  R r1, p1;
+  rho_p_of<EQ, R>(u1, r1, p1, pp);
+  R theta = R(1);
+  const R er = R(0.1) * r0;
+  if (r1 < er) theta = (r0 - er) / (r0 - r1);
+#pragma unroll
+  for (int v = 0; v < M; ++v) u1[v] = u0[v] + theta * du[v];
+  R rt, pt;
+  rho_p_of<EQ, R>(u1, rt, pt, pp);
+  const R ep = R(0.1) * p0;
+  if (pt < ep) theta = theta * (p0 - ep) / (p0 - pt);
+  return theta;
+}
+
+// Limited flux at face node f of the face normal to d between element em
+// ('-', its xi_d = 1 side) and ep ('+', its xi_d = 0 side).
+template <class EQ, int N, typename R>
+__device__ __forceinline__ void limited_face_flux(const double* __restrict__ uin, const R* __restrict__ trace,
+                                                  const double* __restrict__ araw, const MeshArgs& ma,
+                                                  const PhysParams<R>& pp, const LimTab& lt, int d, unsigned em,
+                                                  unsigned ep, int f, R dtR, R* F) {
+  constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), C = trace_comps<EQ>();
+  const long long E = ma.E;
+  // time-averaged Rusanov flux from the two records (eq. numflux.cons)
+  R rm[C], rp[C];
+  load_face_record<EQ, N, R>(trace, E, d, 1, f, em, rm);
+  load_face_record<EQ, N, R>(trace, E, d, 0, f, ep, rp);
+  const R lam = fmax(rm[2 * M], rp[2 * M]);
+  R Fho[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) Fho[v] = R(0.5) * (rm[M + v] + rp[M + v]) - R(0.5) * lam * (rp[v] - rm[v]);
+  // u^n traces and the neighbouring interior nodes
+  const int stride = ipow(n, d);
+  const int fb = line_base<n>(f, stride);
+  R um[M], up[M], umi[M], upi[M];
+  load_node<M, R>(uin, E, em, NP, fb + N * stride, um);
+  load_node<M, R>(uin, E, ep, NP, fb, up);
+  load_node<M, R>(uin, E, em, NP, fb + (N - 1) * stride, umi);
+  load_node<M, R>(uin, E, ep, NP, fb + stride, upi);
+  R flo[M];
+  rusanov_lo<EQ, R>(d, um, up, flo, pp);
+  const double af64 = 0.5 * (alpha_smoothed<DIM>(araw, em, ma) + alpha_smoothed<DIM>(araw, ep, ma));
+  const R af = dt_as<R>(af64);
+  R Fb[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) Fb[v] = af64 >= 1.0 ? flo[v] : (R(1) - af) * Fho[v] + af * flo[v];
+  if (!(af64 > 0.0)) {
+#pragma unroll
+    for (int v = 0; v < M; ++v) F[v] = Fb[v];
+    return;
+  }
+  // one-direction low-order states of the two end subcells with f_lo and the
+  // change the blend would make to them
+  R fmi[M], fpi[M];
+  rusanov_lo<EQ, R>(d, umi, um, fmi, pp);
+  rusanov_lo<EQ, R>(d, up, upi, fpi, pp);
+  const R idx = inv_dx_of<R>(ma, d);
+  const R cm = R(DIM) * dtR * idx / R(lt.w01[N]), cp = R(DIM) * dtR * idx / R(lt.w01[0]);
+  R lm[M], dm[M], lp[M], dp[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    lm[v] = um[v] - cm * (flo[v] - fmi[v]);
+    dm[v] = -cm * (Fb[v] - flo[v]);
+    lp[v] = up[v] - cp * (fpi[v] - flo[v]);
+    dp[v] = cp * (Fb[v] - flo[v]);
+  }
+  const R theta = fmin(admissible_theta<EQ, R>(lm, dm, pp), admissible_theta<EQ, R>(lp, dp, pp));
+#pragma unroll
+  for (int v = 0; v < M; ++v) F[v] = flo[v] + theta * (Fb[v] - flo[v]);
+}
+
+// ---------------------------------------------------------------------------
+// Limited face / update kernel: one thread per node
+// ---------------------------------------------------------------------------
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(256)
+k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
+                      const R* __restrict__ trace, const double* __restrict__ araw, DevState* __restrict__ st,
+                      const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot) {
+  constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), NF = NP / n;
+  constexpr bool F32 = sizeof(R) == 4;
+  const long long E = ma.E;
+  if (st->status & ST_TIMEOUT) return;
+  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+  R lam = R(0);
+  bool bad = false;
+  if (gid < (unsigned)(E * NP)) {
+    const unsigned e = gid / NP;
+    const int p = (int)(gid % NP);
+    unsigned ec[3] = {0, 0, 0};
+    elem_coords<DIM>(e, ma, ec);
+    const R dtR = step_dt<R>(st);
+    const double ae = alpha_smoothed<DIM>(araw, e, ma);
+    R uc[M];
+    load_node<M, R>(uin, E, e, NP, p, uc);
+    // high-order increment (eq. crkfr.non.cons.final) and first-order subcell increment
+    R dh[M], dl[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      dh[v] = -dtR * rbar[((size_t)v * E + e) * NP + p];
+      dl[v] = R(0);
+    }
+    int rem = p;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int cd = rem % n;
+      rem /= n;
+      const int stride = ipow(n, d);
+      const int f = (p % stride) + (p / (stride * n)) * stride;
+      const R idx = inv_dx_of<R>(ma, d);
+      R fl[M], fr[M];
+      if (cd > 0) {
+        R un[M];
+        load_node<M, R>(uin, E, e, NP, p - stride, un);
+        rusanov_lo<EQ, R>(d, un, uc, fl, pp);
+      }
+      if (cd < N) {
+        R un[M];
+        load_node<M, R>(uin, E, e, NP, p + stride, un);
+        rusanov_lo<EQ, R>(d, uc, un, fr, pp);
+      }
+      if (cd == N) {   // face xi_d = 1: this element is '-'
+        R F[M];
+        limited_face_flux<EQ, N, R>(uin, trace, araw, ma, pp, lt, d, e, neighbour_of(e, ec, d, +1, ma), f, dtR, F);
+        const R s = dtR * tb.iwN * idx;
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          dh[v] -= s * (F[v] - trace[trace_index<EQ, NF>(d, 1, f, M + v, E, e)]);
+          fr[v] = F[v];
+        }
+      }
+      if (cd == 0) {   // face xi_d = 0: this element is '+'
+        R F[M];
+        limited_face_flux<EQ, N, R>(uin, trace, araw, ma, pp, lt, d, neighbour_of(e, ec, d, -1, ma), e, f, dtR, F);
+        const R s = dtR * tb.iw0 * idx;
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          dh[v] += s * (F[v] - trace[trace_index<EQ, NF>(d, 0, f, M + v, E, e)]);
+          fl[v] = F[v];
+        }
+      }
+      const R c = dtR * idx / R(lt.w01[cd]);
+#pragma unroll
+      for (int v = 0; v < M; ++v) dl[v] -= c * (fr[v] - fl[v]);
+    }
+    // blend of the increments (the low-order one alone where a_e = 1), then
+    // u^{n+1} = u^n + du in FP64
+    const R a = dt_as<R>(ae);
+    double uu[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      const R du = ae >= 1.0 ? dl[v] : (R(1) - a) * dh[v] + a * dl[v];
+      const size_t g = ((size_t)v * E + e) * NP + p;
+      if constexpr (F32) uu[v] = uin[g] + f2d_int(du);
+      else uu[v] = uin[g] + du;
+      uout[g] = uu[v];
+    }
+    bad = !physical_state<EQ, R>(uu, ma, lam);
+  }
+  reduce_lambda<R>(lam, bad, st, slot ^ 1);
+}
+
+}  // namespace crk

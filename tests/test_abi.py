@@ -55,17 +55,17 @@ def test_descriptor_layout_matches_c(tmp_path):
     from paper_2604_02125_gb300 import crkfr
     src = tmp_path / "lay.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "cr.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cr_mesh_desc),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cr_mesh_desc),'
                    'offsetof(cr_mesh_desc, lo), offsetof(cr_mesh_desc, gamma),'
                    'offsetof(cr_mesh_desc, dt_fixed), offsetof(cr_mesh_desc, prec), offsetof(cr_mesh_desc, scheme),'
-                   'offsetof(cr_mesh_desc, ncflux));'
+                   'offsetof(cr_mesh_desc, ncflux), offsetof(cr_mesh_desc, limiter), offsetof(cr_mesh_desc, alpha_max));'
                    ' return 0;}\n')
     exe = tmp_path / "lay"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     D = crkfr.MeshDesc
     assert got == [ctypes.sizeof(D), D.lo.offset, D.gamma.offset, D.dt_fixed.offset, D.prec.offset, D.scheme.offset,
-                   D.ncflux.offset]
+                   D.ncflux.offset, D.limiter.offset, D.alpha_max.offset]
 
 
 def _init_status(lib, mesh, prec="fp64"):
@@ -98,6 +98,15 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
     mh = inputs.mesh_dict("glm_mhd", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 5.0 / 3.0, c_h=1.0)
     d2 = crkfr.make_desc(dict(mh, ncflux="stages"), scheme="rkfr")
     assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL
+    # the subcell blending limiter: Euler, single-stage scheme, 0 <= alpha_max <= 1
+    for m, sch in ((dict(mh, limiter=True), None), (dict(base, limiter=True), "rkfr"),
+                   (dict(base, limiter=True, alpha_max=1.5), None), (dict(base, limiter=True, alpha_max=-0.1), None),
+                   (dict(base, limiter=True, alpha_max=float("nan")), None)):
+        d2 = crkfr.make_desc(m, scheme=sch)
+        assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL, m
+    d2 = crkfr.make_desc(base)
+    d2.limiter = 2
+    assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d2), 1, None) == crkfr.CR_EINVAL
     assert lib.cr_init_mesh(ctypes.byref(h), ctypes.byref(d), 0, None) == crkfr.CR_EINVAL
 
 
@@ -118,6 +127,8 @@ def test_noalloc_size_limit_without_gpu(lib):
     ns = crkfr.make_desc(dict(inputs.mesh_dict("glm_mhd", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 5.0 / 3.0, c_h=1.0),
                               ncflux="stages"))
     assert lib.cr_step_noalloc(ctypes.byref(ns), dummy, dummy, None, None) == crkfr.CR_EINVAL
+    lim = crkfr.make_desc(dict(inputs.mesh_dict("euler", 2, 3, [4, 4], [0, 0], [1.0, 1.0], 1.4), limiter=True))
+    assert lib.cr_step_noalloc(ctypes.byref(lim), dummy, dummy, None, None) == crkfr.CR_EINVAL
     assert lib.cr_step_noalloc(None, dummy, dummy, None, None) == crkfr.CR_EINVAL
 
 
@@ -133,6 +144,8 @@ def _valid(d):
     if d.ncflux != 0 and (d.ncflux != 1 or d.eq != 1 or d.scheme != 0):
         return False
     if not (d.gamma > 1.0) or not (d.cfl > 0.0) or not (d.dt_fixed >= 0.0) or not (d.c_h >= 0.0):
+        return False
+    if d.limiter != 0 and (d.limiter != 1 or d.eq != 0 or d.scheme != 0 or not (0.0 <= d.alpha_max <= 1.0)):
         return False
     nodes = 1
     for k in range(d.dim):
@@ -164,6 +177,7 @@ def test_random_descriptors_rejected_without_gpu(lib):
         d.c_h, d.dt_fixed = pick([0.0, 1.0, -1.0, float("nan")]), pick([0.0, 1e-3, -1.0, float("nan")])
         d.vol, d.surf, d.prec = pick([0, 1, 2, 3]), pick([0, 1]), pick([0, 1, 2])
         d.scheme, d.ncflux = pick([0, 1, 2]), pick([0, 1, 2])
+        d.limiter, d.alpha_max = pick([0, 0, 1, 2]), pick([0.0, 0.5, 1.5, float("nan")])
         if _valid(d):
             continue
         tried += 1
