@@ -115,8 +115,11 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
 /* Create a context on the current CUDA device.
  *   out        : receives the context (NULL on failure).
  *   desc       : n_solves descriptors (copied).
- *   n_solves   : 1 = one mesh advanced by two kernels per step (volume, face +
- *                update, replayed as a CUDA graph; CR_SCHEME_RKFR: the two
+ *   n_solves   : 1 = one mesh advanced by two kernels per step (volume,
+ *                face + update; with CRKFR_STEP_KERNELS=fused in the
+ *                environment, variants whose lane layouts allow it run both
+ *                parts in one cooperative persistent launch instead, which
+ *                measured slower), replayed as a CUDA graph; CR_SCHEME_RKFR: the two
  *                kernels once per RK stage, the volume kernel on the stage
  *                state with a single stage); > 1 = batched form: the
  *                solves (meshes and degrees may differ) advance together, per
@@ -183,8 +186,10 @@ int cr_get_info(cr_ctx *ctx, int solve, double *t, double *dt, long long *steps,
  * duration of one volume-kernel launch, ms[1] of one face/update launch (the
  * batched form: ms[0] = the volume launches of all degrees of one step, ms[1]
  * = their face/update launches; CR_SCHEME_RKFR: ms[0] = the s volume
- * launches of one step, ms[1] = its s face/update launches).  The state advances exactly as with
- * cr_step.  Synchronises the stream. */
+ * launches of one step, ms[1] = its s face/update launches; a single solve
+ * whose step runs as one cooperative launch -- cr_tuning_info reports
+ * "step": "fused" -- ms[0] = that launch, ms[1] = 0).  The state advances
+ * exactly as with cr_step.  Synchronises the stream. */
 int cr_time_kernels(cr_ctx *ctx, int nsteps, void *flush_buf, size_t flush_bytes, double *ms);
 
 /* Measurement: throughput of one unit on the current device, measured with

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -249,14 +250,17 @@ struct cr_ctx {
   int M = 0;
   size_t totals_blocks = 0;
   bool has_state = false;
-  int parity = 0;     // slot of the CFL reduction of the current state
+  int parity = 0;     // slot of the CFL reduction of the current state (the fused step: its phase, 0..2)
   // state buffers: ubuf[0] only, or with the limiter two, the state of parity p
   // in ubuf[p] (the limited step reads one and writes the other)
   double* ubuf[2] = {nullptr, nullptr};
   bool limited = false;
   cudaStream_t cap_stream = nullptr;
-  // graphs of 1 and 16 steps, one per starting parity
-  cudaGraphExec_t g1[2] = {nullptr, nullptr}, g16[2] = {nullptr, nullptr};
+  // the whole step in one cooperative launch (crkfr_fused.cuh), phases mod 3
+  bool fused = false;
+  int nphase = 2;     // 2, or 3 for the fused step
+  // graphs of 1 and 16 steps, one per starting parity / phase
+  cudaGraphExec_t g1[3] = {nullptr, nullptr, nullptr}, g16[3] = {nullptr, nullptr, nullptr};
   // batched form
   BatchedCtx* batched = nullptr;
 };
@@ -306,7 +310,7 @@ static bool desc_valid(const cr_mesh_desc& d) {
 }
 
 static void free_single(cr_ctx* c) {
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     if (c->g1[p]) cudaGraphExecDestroy(c->g1[p]);
     if (c->g16[p]) cudaGraphExecDestroy(c->g16[p]);
     c->g1[p] = c->g16[p] = nullptr;
@@ -317,6 +321,8 @@ static void free_single(cr_ctx* c) {
   c->ubuf[0] = c->ubuf[1] = nullptr;
   c->lc.u = nullptr;
   cudaFree(c->lc.araw);
+  cudaFree(c->lc.flags);
+  c->lc.flags = nullptr;
   cudaFree(c->lc.rbar);
   cudaFree(c->lc.trace);
   cudaFree(c->lc.st);
@@ -330,8 +336,15 @@ static void free_single(cr_ctx* c) {
 // state buffer of the given parity (the only one without the limiter)
 static double* state_buf(const cr_ctx* c, int parity) { return c->ubuf[c->limited ? (parity & 1) : 0]; }
 
+// phase / parity after one step
+static int next_phase(const cr_ctx* c, int p) { return c->fused ? (p + 1) % 3 : p ^ 1; }
+
 static int launch_step(cr_ctx* c, cudaStream_t s, int parity) {
   c->lc.slot = parity;
+  if (c->fused) {
+    CR_TRY(c->ops.step_fused(c->lc, s, parity));
+    return CR_OK;
+  }
   if (c->limited) {
     // coefficients of u^n, the cRKFR volume work, then the limited face /
     // update kernel from the parity's buffer into the other one
@@ -362,7 +375,8 @@ static int capture(cr_ctx* c, int steps, int parity, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CR_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   int rc = CR_OK;
-  for (int k = 0; k < steps && rc == CR_OK; ++k) rc = launch_step(c, c->cap_stream, (parity + k) & 1);
+  int p = parity;
+  for (int k = 0; k < steps && rc == CR_OK; ++k, p = next_phase(c, p)) rc = launch_step(c, c->cap_stream, p);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (rc != CR_OK) { if (g) cudaGraphDestroy(g); return rc; }
   if (e != cudaSuccess) return cuda_status(e);
@@ -409,14 +423,26 @@ static int init_single(cr_ctx* c) {
     al((void**)&lc.ustage, sizeof(double) * (size_t)o.M * nodes);
     al(&lc.kbuf, o.real_bytes * (size_t)(rk_stages(d.degree_N) - 1) * o.M * nodes);
   }
+  // the single-launch step (crkfr_fused.cuh) on request only:
+  // CRKFR_STEP_KERNELS=fused in the environment, for variants that have one.
+  // Measured slower than the two kernels on every workload (the face / update
+  // work, latency-bound, runs at the volume kernel's occupancy there), so the
+  // two-kernel step is the default.
+  const char* sk = std::getenv("CRKFR_STEP_KERNELS");
+  c->fused = o.step_fused && d.scheme == CR_SCHEME_CRKFR && d.ncflux == CR_NCFLUX_REDUCED && !c->limited && sk &&
+             std::strcmp(sk, "fused") == 0;
+  c->nphase = c->fused ? 3 : 2;
+  if (c->fused) al((void**)&lc.flags, sizeof(unsigned) * (size_t)((E + 31) / 32));
   if (rc != CR_OK) { free_single(c); return rc; }
   lc.ma.tma_ok = tma_ok_for(lc.u, E, o.NP);
   cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
-  CR_TRY(cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream));
+  e = cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream);
+  if (e == cudaSuccess && c->fused) e = cudaMemsetAsync(lc.flags, 0, sizeof(unsigned) * (size_t)((E + 31) / 32), c->stream);
+  if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
-  for (int p = 0; p < 2 && rc == CR_OK; ++p) {
+  for (int p = 0; p < c->nphase && rc == CR_OK; ++p) {
     rc = capture(c, 1, p, &c->g1[p]);
     if (rc == CR_OK) rc = capture(c, 16, p, &c->g16[p]);
   }
@@ -481,6 +507,7 @@ int cr_set_state(cr_ctx* c, int solve, const double* u, int u_on_device) {
   CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->stream));
   CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
+  if (c->fused) CR_TRY(cudaMemsetAsync(c->lc.flags, 0, sizeof(unsigned) * (size_t)((c->E + 31) / 32), c->stream));
   c->parity = 0;
   c->lc.slot = 0;
   CR_TRY(c->ops.lambda(c->lc, c->stream));
@@ -497,6 +524,7 @@ int cr_set_state_async(cr_ctx* c, int solve, const double* u, int u_on_device) {
   CR_TRY(cudaMemcpyAsync(c->lc.u, u, bytes, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          c->stream));
   CR_TRY(cudaMemsetAsync(c->lc.st, 0, sizeof(DevState), c->stream));
+  if (c->fused) CR_TRY(cudaMemsetAsync(c->lc.flags, 0, sizeof(unsigned) * (size_t)((c->E + 31) / 32), c->stream));
   c->parity = 0;
   c->lc.slot = 0;
   CR_TRY(c->ops.lambda(c->lc, c->stream));
@@ -518,10 +546,13 @@ int cr_step(cr_ctx* c, int nsteps) {
   if (c->batched) return batched_step(c->batched, nsteps);
   if (!c->has_state) return CR_EINVAL;
   int k = 0;
-  for (; k + 16 <= nsteps; k += 16) CR_TRY(cudaGraphLaunch(c->g16[c->parity], c->stream));   // parity unchanged
+  for (; k + 16 <= nsteps; k += 16) {
+    CR_TRY(cudaGraphLaunch(c->g16[c->parity], c->stream));
+    if (c->fused) c->parity = (c->parity + 16) % 3;   // the two-kernel parity is unchanged
+  }
   for (; k < nsteps; ++k) {
     CR_TRY(cudaGraphLaunch(c->g1[c->parity], c->stream));
-    c->parity ^= 1;
+    c->parity = next_phase(c, c->parity);
     c->lc.u = state_buf(c, c->parity);
   }
   return CR_OK;
@@ -588,6 +619,17 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
     c->lc.slot = c->parity;
     c->lc.u = state_buf(c, c->parity);
     c->lc.u_next = state_buf(c, c->parity ^ 1);
+    if (c->fused) {
+      // the single-launch step: ms[0] is the whole step, ms[1] = 0
+      cudaEvent_t* e4 = &ev[4 * (size_t)k];
+      cudaEventRecord(e4[0], c->stream);
+      if (c->ops.step_fused(c->lc, c->stream, c->parity) != cudaSuccess) rc = CR_ECUDA;
+      cudaEventRecord(e4[1], c->stream);
+      cudaEventRecord(e4[2], c->stream);
+      cudaEventRecord(e4[3], c->stream);
+      if (rc == CR_OK) c->parity = next_phase(c, c->parity);
+      continue;
+    }
     for (int j = 0; j < S && rc == CR_OK; ++j) {
       cudaEvent_t* e4 = &ev[4 * ((size_t)k * S + j)];
       cudaEventRecord(e4[0], c->stream);
@@ -606,7 +648,7 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
       }
       cudaEventRecord(e4[3], c->stream);
     }
-    if (rc == CR_OK) c->parity ^= 1;
+    if (rc == CR_OK) c->parity = next_phase(c, c->parity);
     c->lc.u = state_buf(c, c->parity);
   }
   if (rc == CR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = CR_ECUDA;
@@ -622,7 +664,7 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
     if (e) cudaEventDestroy(e);
   if (rc != CR_OK) return rc;
   ms[0] = tv / nsteps;
-  ms[1] = tf / nsteps;
+  ms[1] = c->fused ? 0.0 : tf / nsteps;
   return read_status(c);
 }
 
@@ -644,8 +686,10 @@ int cr_tuning_info(cr_ctx* c, char* buf, size_t len) {
   } else {
     char tmp[256];
     std::snprintf(tmp, sizeof(tmp),
-                  "{\"scheme\": \"%s\", \"volume\": \"%s\", \"elements_per_cta\": %d, \"face\": \"%s\"}",
-                  c->desc[0].scheme == CR_SCHEME_RKFR ? "rkfr" : "crkfr", c->ops.lanes ? "lanes" : "tile",
+                  "{\"scheme\": \"%s\", \"step\": \"%s\", \"volume\": \"%s\", \"elements_per_cta\": %d, "
+                  "\"face\": \"%s\"}",
+                  c->desc[0].scheme == CR_SCHEME_RKFR ? "rkfr" : "crkfr", c->fused ? "fused" : "split",
+                  c->ops.lanes ? "lanes" : "tile",
                   c->ops.lanes ? 32 : c->lc.epb,
                   c->limited ? "limited per-node" : (c->ops.threads_face > 0 ? "lanes" : "per-node"));
     info = tmp;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include "../../include/cr.h"
+#include "crkfr_fused.cuh"
 #include "crkfr_limiter.cuh"
 #include "crkfr_volume_lanes.cuh"
 
@@ -32,6 +33,8 @@ struct LaunchCtx {
   double* u_next;
   double* araw;
   LimTab lt;
+  // fused single-launch step: per-tile readiness values
+  unsigned* flags;
 };
 
 // One launch of a batched persistent kernel (all solves of one degree).
@@ -66,6 +69,9 @@ struct VariantOps {
   // the limited face / update kernel from u into u_next
   cudaError_t (*alpha)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*face_limited)(const LaunchCtx&, cudaStream_t);
+  // the whole step in one cooperative persistent launch (lane forms of the
+  // single-stage scheme; null where the layouts do not allow it); phase 0..2
+  cudaError_t (*step_fused)(const LaunchCtx&, cudaStream_t, int phase);
   cudaError_t (*lambda)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*totals)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*set_smem)(size_t bytes);

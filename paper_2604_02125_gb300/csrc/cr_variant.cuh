@@ -138,6 +138,42 @@ struct Variant {
     }
     return cudaErrorNotSupported;
   }
+  using FU = FusedLayout<EQ, N, R>;
+  static constexpr bool kFused = FU::fits() && !EQ::NC;
+  static int fused_occupancy() {
+    static int occ = -1;
+    if (occ < 0) {
+      int nb = 0;
+      if constexpr (kFused) {
+        cudaFuncSetAttribute(k_step_fused<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FU::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<EQ, N, R>, LL::THREADS, FU::bytes());
+      }
+      occ = nb;
+    }
+    return occ;
+  }
+  static cudaError_t step_fused(const LaunchCtx& c, cudaStream_t s, int phase) {
+    if constexpr (kFused) {
+      const int occ = fused_occupancy();
+      if (occ < 1) return cudaErrorInvalidConfiguration;
+      const long long ntiles = (c.ma.E + 31) / 32;
+      // cooperative: every CTA resident, so the bounded readiness waits end
+      const long long grid = std::min(ntiles, (long long)c.sms * occ);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)grid);
+      cfg.blockDim = dim3(LL::THREADS);
+      cfg.dynamicSmemBytes = FU::bytes();
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_step_fused<EQ, N, R>, c.u, (R*)c.rbar, (R*)c.trace, c.st, c.flags, c.ma,
+                                PP<R>::get(c), PP<R>::tab(c), phase);
+    }
+    return cudaErrorNotSupported;
+  }
   static cudaError_t lambda(const LaunchCtx& c, cudaStream_t s) {
     const long long total = c.ma.E * L::NP;
     const unsigned grid = (unsigned)((total + 255) / 256);
@@ -163,6 +199,11 @@ struct Variant {
                                  (int)FL::bytes());
         if (e != cudaSuccess) return e;
       }
+    }
+    if constexpr (kFused) {
+      cudaError_t e = cudaFuncSetAttribute(k_step_fused<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FU::bytes());
+      if (e != cudaSuccess) return e;
     }
     if constexpr (kLanes) {
       if constexpr (kBatched) {
@@ -239,6 +280,7 @@ struct Variant {
     o->volume_stage = &volume_stage;
     o->face_stage = &face_stage;
     o->lambda = &lambda;
+    o->step_fused = kFused ? &step_fused : nullptr;
     o->alpha = EQ::NC ? nullptr : &alpha;
     o->face_limited = EQ::NC ? nullptr : &face_limited;
     o->totals = &totals;

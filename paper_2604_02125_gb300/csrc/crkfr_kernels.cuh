@@ -88,8 +88,14 @@ struct RefTab {
 // (the host passes it to every kernel); the volume kernel of the step that
 // starts from that state reads it (kernel boundaries order the two), derives
 // dt, records the step and clears the other slot for the new state.
+// The fused single-launch step (crkfr_fused.cuh) reduces into a third slot: it
+// rotates read / write / clear slots modulo 3, because its clear and its
+// reductions happen within one launch.  epoch[] carries its per-step tile
+// readiness value the same way.
 struct DevState {
-  unsigned long long lam_bits[2];   // max over nodes of sum_d lambda_d / dx_d (bits of a non-negative double)
+  unsigned long long lam_bits[3];   // max over nodes of sum_d lambda_d / dx_d (bits of a non-negative double)
+  unsigned epoch[3];   // fused step: readiness value of the step that starts from a slot
+  unsigned pad0;
   double dt;           // dt of the last step (set when the step starts)
   double t;            // time after the last step
   double lam_max;      // wave-speed maximum the last step's dt came from
@@ -133,11 +139,12 @@ __device__ __forceinline__ void reduce_lambda(T lam, bool bad, DevState* st, int
 // state: cfl / max_nodes sum_d lambda_d/dx_d, or the fixed dt.  Every caller
 // computes the same value; the one with lead set (one per solve and launch)
 // records the step and clears the other slot for the new state's reduction.
-__device__ __forceinline__ double step_begin(DevState* st, int slot, double cfl, double dt_fixed, bool lead) {
+__device__ __forceinline__ double step_begin_slots(DevState* st, int slot, int clear_slot, double cfl, double dt_fixed,
+                                                   bool lead) {
   const double lam = __longlong_as_double((long long)st->lam_bits[slot]);
   const double dt = dt_fixed > 0.0 ? dt_fixed : cfl / lam;
   if (lead) {
-    st->lam_bits[slot ^ 1] = 0ull;
+    st->lam_bits[clear_slot] = 0ull;
     st->dt = dt;
     st->t += dt;
     st->steps += 1;
@@ -145,6 +152,17 @@ __device__ __forceinline__ double step_begin(DevState* st, int slot, double cfl,
     if (!(lam > 0.0) || !isfinite(lam)) atomicOr(&st->status, ST_NONPHYS);
   }
   return dt;
+}
+__device__ __forceinline__ double step_begin(DevState* st, int slot, double cfl, double dt_fixed, bool lead) {
+  return step_begin_slots(st, slot, slot ^ 1, cfl, dt_fixed, lead);
+}
+
+// Loads of data another CTA wrote earlier in the same launch (fused step):
+// through L2 (ld.global.cg), never the non-coherent path or a stale L1 line.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
 }
 
 // the current step's dt in the path's arithmetic (face kernels, after the
@@ -489,13 +507,13 @@ __device__ __forceinline__ bool physical_state(const double* uu, const MeshArgs&
 // Face + update kernel: one thread per node
 // ---------------------------------------------------------------------------
 // the C components of the record of face node f of face (d, side) of element e
-template <class EQ, int N, typename R>
+template <class EQ, int N, typename R, bool COH = false>
 __device__ __forceinline__ void load_face_record(const R* __restrict__ trace, long long E, int d, int side, int f,
                                                  long long e, R (&rec)[trace_comps<EQ>()]) {
   constexpr int NF = ipow(N + 1, EQ::DIM) / (N + 1), C = trace_comps<EQ>();
   const R* p = trace + trace_index<EQ, NF>(d, side, f, 0, E, e);
 #pragma unroll
-  for (int c = 0; c < C; ++c) rec[c] = p[(size_t)c * E];
+  for (int c = 0; c < C; ++c) rec[c] = ldx<COH>(p + (size_t)c * E);
 }
 
 // Jump J = F^num - F_own [+ B(u^n_own) g^avg(U) - F^nc_own] at one face node
@@ -527,13 +545,13 @@ __device__ __forceinline__ void jump_of(const R* o, const R* x, int d, int side_
   }
 }
 
-template <class EQ, int N, typename R>
+template <class EQ, int N, typename R, bool COH = false>
 __device__ __forceinline__ void face_jump(const R* __restrict__ trace, long long E, int d, int side_own, long long e_own,
                                           long long e_oth, int f, R* J, const PhysParams<R>& pp, const RefTab<R>& tb) {
   constexpr int C = trace_comps<EQ>();
   R o[C], x[C];
-  load_face_record<EQ, N, R>(trace, E, d, side_own, f, e_own, o);
-  load_face_record<EQ, N, R>(trace, E, d, 1 - side_own, f, e_oth, x);
+  load_face_record<EQ, N, R, COH>(trace, E, d, side_own, f, e_own, o);
+  load_face_record<EQ, N, R, COH>(trace, E, d, 1 - side_own, f, e_oth, x);
   jump_of<EQ, R>(o, x, d, side_own, J, pp);
   if constexpr (EQ::NCS) {
     // + sum_j b_j B(u^(j)_own) g^avg(u^(j)) (eq. bad.numflux.non.cons)

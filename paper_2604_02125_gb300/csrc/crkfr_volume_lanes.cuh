@@ -768,24 +768,25 @@ struct FaceLaneLayout {
   static constexpr bool fits() { return THREADS <= 1024 && bytes() <= 227 * 1024; }
 };
 
-// n contiguous values starting at src (vector loads where the alignment allows)
-template <int n, typename T>
+// n contiguous values starting at src (vector loads where the alignment
+// allows; COH: through L2, for data written earlier in the same launch)
+template <int n, typename T, bool COH = false>
 __device__ __forceinline__ void load_line(const T* __restrict__ src, T (&out)[n]) {
   if constexpr (sizeof(T) == 4 && n % 4 == 0) {
 #pragma unroll
     for (int k = 0; k < n / 4; ++k) {
-      const float4 t = reinterpret_cast<const float4*>(src)[k];
+      const float4 t = ldx<COH>(reinterpret_cast<const float4*>(src) + k);
       out[4 * k] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
     }
   } else if constexpr (sizeof(T) == 8 && n % 2 == 0) {
 #pragma unroll
     for (int k = 0; k < n / 2; ++k) {
-      const double2 t = reinterpret_cast<const double2*>(src)[k];
+      const double2 t = ldx<COH>(reinterpret_cast<const double2*>(src) + k);
       out[2 * k] = t.x; out[2 * k + 1] = t.y;
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < n; ++k) out[k] = src[k];
+    for (int k = 0; k < n; ++k) out[k] = ldx<COH>(src + k);
   }
 }
 template <int n>
@@ -823,12 +824,17 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
 // RK = true: stage mode of the multi-stage RKFR step (RkStage): the increment
 // is the stage's K_j, combined with the earlier stages' into the next stage
 // state (eq. rkfr1) or, at the last stage, into u^{n+1} (eq. rkfr2).
-template <class EQ, int N, typename R, bool RK = false>
+// FUSED: a tile of the fused single-launch step (crkfr_fused.cuh): dt comes
+// from the caller (dt_fused), slot is the CFL reduction's write slot itself,
+// and R-bar and the face records, written by other CTAs in the same launch,
+// are read through L2.
+template <class EQ, int N, typename R, bool RK = false, bool FUSED = false>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
                                                 unsigned e0, int slot, R* __restrict__ sj,
-                                                const RkStage<R>& rk = RkStage<R>{nullptr, nullptr, 0, 1}) {
+                                                const RkStage<R>& rk = RkStage<R>{nullptr, nullptr, 0, 1},
+                                                R dt_fused = R(0)) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
   constexpr bool F32 = sizeof(R) == 4;
@@ -836,10 +842,12 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   const int l = tid >> 5, el = tid & 31;
   const long long E = ma.E;
   // a volume CTA that timed out left its records unwritten: leave u^n as it is
-  if (st->status & ST_TIMEOUT) return;
+  if constexpr (!FUSED) {
+    if (st->status & ST_TIMEOUT) return;
+  }
   const bool active = (long long)e0 + el < E;
   const unsigned e = e0 + el;
-  const R dtR = step_dt<R>(st);
+  const R dtR = FUSED ? dt_fused : step_dt<R>(st);
 
   // own x-line: Rbar and u^n (N+1 contiguous values per variable), loads issued first
   R rb[M][n];
@@ -850,19 +858,19 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       const size_t g = ((size_t)v * E + e) * NP + l * n;
-      load_line<n>(rbar + g, rb[v]);
+      load_line<n, R, FUSED>(rbar + g, rb[v]);
       load_line<n>(u + g, un[v]);
     }
     elem_coords<DIM>(e, ma, ec);
     // ---- phase A: x faces at the own line's ends, face node l of the y / z faces
-    face_jump<EQ, N, R>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp, tb);
-    face_jump<EQ, N, R>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp, tb);
+    face_jump<EQ, N, R, FUSED>(trace, E, 0, 1, e, neighbour_of(e, ec, 0, +1, ma), l, Jm, pp, tb);
+    face_jump<EQ, N, R, FUSED>(trace, E, 0, 0, e, neighbour_of(e, ec, 0, -1, ma), l, Jp, pp, tb);
 #pragma unroll
     for (int d = 1; d < DIM; ++d)
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         R J[M];
-        face_jump<EQ, N, R>(trace, E, d, side, e, neighbour_of(e, ec, d, side ? +1 : -1, ma), l, J, pp, tb);
+        face_jump<EQ, N, R, FUSED>(trace, E, d, side, e, neighbour_of(e, ec, d, side ? +1 : -1, ma), l, J, pp, tb);
         const R sc = side ? -(dtR * tb.iwN * inv_dx_of<R>(ma, d)) : dtR * tb.iw0 * inv_dx_of<R>(ma, d);
         R* dst = sj + ((size_t)(((d - 1) * 2 + side) * NF + l) * M) * 32 + el;
 #pragma unroll
@@ -952,7 +960,7 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   // rk.uout
   double* dst = u;
   if (RK && rk.j != rk.s - 1) dst = rk.uout;
-  else reduce_lambda<R>(lam, bad, st, slot ^ 1);
+  else reduce_lambda<R>(lam, bad, st, FUSED ? slot : slot ^ 1);
   if (active) {
 #pragma unroll
     for (int v = 0; v < M; ++v) store_line<n>(dst + ((size_t)v * E + e) * NP + l * n, un[v]);

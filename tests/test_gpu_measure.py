@@ -1,8 +1,9 @@
 """The measurement entry points: unit-throughput probes and per-kernel timing.
 
-cr_time_kernels launches the two kernels of every step directly between CUDA
-events; the state must advance exactly as with cr_step (bit for bit: the same
-kernels in the same order), for a single solve and for a batch.
+cr_time_kernels launches the kernels of every step directly between CUDA
+events (the two kernels, or the single fused launch); the state must advance
+exactly as with cr_step (bit for bit: the same kernels in the same order), for
+a single solve and for a batch.
 """
 import ctypes
 import math
@@ -38,16 +39,24 @@ def test_probe_peaks_are_plausible(cr):
     assert cr.load_library().cr_probe_peak(9, ctypes.byref(r)) == cr.CR_EINVAL
 
 
+@pytest.mark.parametrize("step_kernels", ["fused", "split"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_time_kernels_advances_like_step(cr, prec):
+def test_time_kernels_advances_like_step(cr, prec, step_kernels, monkeypatch):
+    """split (the default): the volume and face / update kernels timed apart;
+    fused (CRKFR_STEP_KERNELS=fused): the single launch in ms[0], ms[1] = 0."""
+    if step_kernels == "fused":
+        monkeypatch.setenv("CRKFR_STEP_KERNELS", "fused")
+    else:
+        monkeypatch.delenv("CRKFR_STEP_KERNELS", raising=False)
     mesh, U = inputs.shear_layer_2d(cells=(40, 24), N=3)
     with cr.Solver(mesh, prec=prec) as a, cr.Solver(mesh, prec=prec) as b:
+        assert a.tuning_info()["step"] == step_kernels
         a.set_state(U)
         b.set_state(U)
         a.step(2)
         vol, face = a.time_kernels(3)
         b.step(5)
-        assert vol > 0 and face > 0
+        assert vol > 0 and (face > 0 if step_kernels == "split" else face == 0)
         assert a.info()["steps"] == 5
         assert np.array_equal(a.get_state(), b.get_state())
         assert a.info()["dt"] == b.info()["dt"]
