@@ -44,22 +44,14 @@ def _peaks():
         return {}
 
 
-# Algorithmic FP32 work of the volume kernel, counted from the formulas (an
-# add or multiply is one flop, an FMA two, a reciprocal one; compares zero):
-#   per Ranocha pair flux in 2D (series branch of the logarithmic means):
-#     both log-means 35, averages and the flux 22, accumulation into the two
-#     nodes with 2 D_pq and 2 D_qp 18  ->  75 flops;
-#   per node and stage: pair data 11, stage combination and Rbar 24, the two
-#     end-point fluxes of each line 18, residual scaling 8  ->  61 flops.
-FLOPS_PER_PAIR_2D = 75
-FLOPS_PER_NODE_STAGE_2D = 61
-
-
+# Algorithmic work of the volume kernel (flops counted from the formulas) and
+# of the face / update kernel (bytes): paper_2604_02125_gb300/work.py.  2D
+# Euler, EC flux: 75 flops per pair flux, 61 per node and stage.
 def volume_flops_2d(E, N, stages):
-    n = N + 1
-    pairs = E * stages * 2 * n * (n * (n - 1) // 2)
-    nodes = E * n * n
-    return pairs * FLOPS_PER_PAIR_2D + nodes * stages * FLOPS_PER_NODE_STAGE_2D
+    from paper_2604_02125_gb300 import work
+    side = int(round(E ** 0.5))
+    mesh = {"eq": "euler", "dim": 2, "N": N, "cells": [side, E // side], "vol": "ec"}
+    return work.volume_flops(mesh, stages)
 
 
 class ClockSampler:
@@ -246,7 +238,6 @@ def run_batched(crkfr, inputs, stream, steps):
     b = crkfr.Solver(meshes, prec="fp32", stream=stream)
     for k, (_, U) in enumerate(solves):
         b.set_state(U, solve=k)
-    del solves
     b.step(2)                      # autotune + graph capture happen here
     b.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -259,6 +250,10 @@ def run_batched(crkfr, inputs, stream, steps):
     info = b.tuning_info()
     status = b.info(solve=0)["status"]
     b.close()
+    # the same solves one after another through single-solve contexts: what
+    # the persistent per-degree kernels and their autotuning gain
+    from paper_2604_02125_gb300.measure_configs import sequential_batch
+    seq = sequential_batch(meshes, [U for _, U in solves], steps, stream)
     # roofline of the per-degree volume kernels: counted FP32 flops of every
     # solve of that degree / the kernel's autotuned launch time
     stages = {1: 2, 2: 3, 3: 4, 4: 6, 5: 7}
@@ -275,6 +270,7 @@ def run_batched(crkfr, inputs, stream, steps):
                                    "gflop_per_launch": f / 1e9, "ms_per_launch": t}
     return {"value": nodes / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "solves": len(meshes),
             "nodes": nodes, "status": crkfr.status_string(status), "tuning": info,
+            "vs_sequential": seq["ms_per_step"] / ms, "sequential": seq,
             "volume_roofline": dict(vol_roof, bound="alu", peak_tflops=fp32_peak,
                                     note="launch times from the autotuner (best of two, warm L2)"),
             "workload": "512 independent 2D Euler solves, sides 16..128 quads, N in {2,3,4,5}, seeded smooth "
@@ -418,10 +414,28 @@ def main():
         e64.step(100)
         a32, a64 = e32.get_state(), e64.get_state()
         err100 = float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64))
+        time32, time64 = e32.info()["t"], e64.info()["t"]
         e32.close()
         e64.close()
 
         batched = None if args.no_batched else run_batched(crkfr, inputs, stream, max(3, min(10, args.steps)))
+
+        # the subcell blending limiter with the paper's Kelvin-Helmholtz
+        # setting (KEP volume flux, alpha_max = 0.008) on the same mesh,
+        # against the unlimited step with the same flux
+        mk, Uk = inputs.shear_layer_2d(cells=CELLS, N=N_DEG, vol="kep")
+        lim = {}
+        kl = max(3, min(200, args.steps))
+        for tag, m in (("limited", dict(mk, limiter=True, alpha_max=0.008)), ("unlimited", mk)):
+            r = crkfr.Solver(m, prec="fp32", stream=stream)
+            r.set_state(Uk)
+            r.step(2)
+            r.sync()
+            tl = time_steps(r, kl, stream, flush)
+            lim[tag] = {"ms_per_step": sum(tl) / kl, "value": nodes * kl / (sum(tl) * 1e-3), "steps": kl,
+                        "status": crkfr.status_string(r.info()["status"])}
+            r.close()
+        lim["cost"] = lim["limited"]["ms_per_step"] / lim["unlimited"]["ms_per_step"]
 
         # the multi-stage RKFR scheme (eq. rkfr.non.cons) on the same workload
         # and kernels: s volume and s face exchanges per step, against one
@@ -552,7 +566,14 @@ def main():
         "gpu_launches": 2 * args.steps,
         "status": crkfr.status_string(status),
         "forms": {"fp32_pairflux": {"value": value, "ms_per_step": ms_step,
-                                    "rel_l2_vs_fp64_after_100_steps": err100},
+                                    "rel_l2_vs_fp64_after_100_steps": err100,
+                                    "rel_t_vs_fp64_after_100_steps": abs(time32 - time64) / time64,
+                                    "dt": "FP64 maximum and division, FP32 wave speeds of the FP64 state (reading "
+                                          "R15): dt within 1e-6 of the oracle's per step"},
+                  "limiter": dict(lim, setting="KEP volume flux, subcell blending limiter alpha_max = 0.008 (the "
+                                               "paper's Kelvin-Helmholtz runs), FP32 form; per step the coefficient "
+                                               "kernel, the volume kernel and the limited per-node face / update kernel",
+                                  rel_l2_vs_oracle="<= 1e-12 per step (FP64), tests/test_gpu_limiter.py"),
                   "fp64": {"value": nodes * k64 / (sum(t64) * 1e-3), "ms_per_step": sum(t64) / k64, "steps": k64,
                            "rel_l2_vs_oracle_per_step": "<= 1e-12 (tests/test_gpu_parity.py)"},
                   "batched": batched,
@@ -575,7 +596,7 @@ def main():
                 "sequential": {"value": world * nodes * kq / seq_s, "steps": kq,
                                "mode": "one context, cr_set_state / cr_step / cr_get_state (synchronous)"}},
         "roofline": roofline,
-        "clocks": dict(clocks, window="headline, fp64, batched, rkfr and per-kernel timed regions") if clocks else None,
+        "clocks": dict(clocks, window="headline, fp64, batched, limiter, rkfr and per-kernel timed regions") if clocks else None,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()

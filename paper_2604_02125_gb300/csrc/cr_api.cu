@@ -321,6 +321,7 @@ static void free_single(cr_ctx* c) {
   c->ubuf[0] = c->ubuf[1] = nullptr;
   c->lc.u = nullptr;
   cudaFree(c->lc.araw);
+  cudaFree(c->lc.alpha);
   cudaFree(c->lc.flags);
   c->lc.flags = nullptr;
   cudaFree(c->lc.rbar);
@@ -412,6 +413,7 @@ static int init_single(cr_ctx* c) {
   if (c->limited) {
     al((void**)&c->ubuf[1], sizeof(double) * (size_t)o.M * nodes);
     al((void**)&lc.araw, sizeof(double) * (size_t)E);
+    al((void**)&lc.alpha, sizeof(double) * (size_t)E);
     fill_lim_tab(d.degree_N, d.alpha_max, &lc.lt);
   }
   lc.u = c->ubuf[0];

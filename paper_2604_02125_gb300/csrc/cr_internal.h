@@ -32,6 +32,7 @@ struct LaunchCtx {
   // the coefficients before smoothing (one per element) and the tables
   double* u_next;
   double* araw;
+  double* alpha;      // smoothed coefficients
   LimTab lt;
   // fused single-launch step: per-tile readiness values
   unsigned* flags;

@@ -124,16 +124,29 @@ struct Variant {
     if constexpr (!EQ::NC) {
       const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
       k_alpha_raw<EQ, N><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
+      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.ma);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
   }
+  // the limited face / update part: the lane kernel for the elements the
+  // limiter does not touch, the per-node limited kernel for the others (all
+  // elements where the lane layout does not fit)
   static cudaError_t face_limited(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (!EQ::NC) {
+      if constexpr (kFaceLanes) {
+        const unsigned tiles = (unsigned)((c.ma.E + 31) / 32);
+        k_face_update_lanes_clean<EQ, N, R><<<tiles, FL::THREADS, FL::bytes(), s>>>(
+            c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.alpha, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c),
+            c.slot);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
       const long long total = c.ma.E * L::NP;
       const unsigned grid = (unsigned)((total + 255) / 256);
-      k_face_update_limited<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.araw,
-                                                           c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt, c.slot);
+      k_face_update_limited<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.alpha,
+                                                           c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt, c.slot,
+                                                           kFaceLanes ? 1 : 0);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -194,6 +207,11 @@ struct Variant {
       e = cudaFuncSetAttribute(k_face_stage_lanes<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)FL::bytes());
       if (e != cudaSuccess) return e;
+      if constexpr (!EQ::NC) {
+        e = cudaFuncSetAttribute(k_face_update_lanes_clean<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FL::bytes());
+        if (e != cudaSuccess) return e;
+      }
       if constexpr (kBatched) {
         e = cudaFuncSetAttribute(k_face_batched<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)FL::bytes());

@@ -6,11 +6,17 @@
 //                        rho p (energy fraction of the highest orthonormal
 //                        Legendre modes), the logistic map, its clips and the
 //                        cap alpha_max.  One thread per element.
+//  k_alpha_smooth        per element: a_e = max(raw_e, raw_nb / 2 over the
+//                        face neighbours).
 //  k_face_update_limited per node: the cRKFR update u^H with the limited face
 //                        flux at element faces, the first-order subcell update
 //                        u^L with the same face flux, the blend
 //                        (1 - a_e) u^H + a_e u^L into the other state buffer,
-//                        and the CFL reduction of the result.
+//                        and the CFL reduction of the result.  Where the lane
+//                        face kernel exists it takes the elements the limiter
+//                        does not touch (a = 0 there and at every face
+//                        neighbour: the plain update, k_face_update_lanes_clean)
+//                        and this kernel only the others.
 //
 // The limited face flux at a face node between elements '-' and '+':
 //   F_blend = (1 - a_f) F^num + a_f f_lo   (f_lo alone where a_f = 1),
@@ -21,8 +27,6 @@
 //   subcells' one-direction low-order states at or above a tenth of their
 //   values with f_lo.  Both elements evaluate it from the same '-'/'+' data
 //   in the same order, so they get the same bits and the step conserves.
-// The smoothed coefficient a_e = max(raw_e, raw_nb / 2 over the face
-// neighbours) is formed where it is used, from k_alpha_raw's values.
 //
 // u^n is read from one state buffer and u^{n+1} written to the other (the
 // first-order fluxes read neighbouring nodes of other elements), so a limited
@@ -67,8 +71,6 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
   // modal coefficients: the 1D transform along every direction in turn
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    constexpr int dummy = 0;
-    (void)dummy;
     const int stride = ipow(n, d);
 #pragma unroll 1
     for (int l = 0; l < NP / n; ++l) {
@@ -109,18 +111,21 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
   araw[e] = fmin(a, lt.alpha_max);
 }
 
-// smoothed coefficient of element e: max(raw_e, raw_nb / 2 over the face neighbours)
+// smoothed coefficient per element: max(raw_e, raw_nb / 2 over the face neighbours)
 template <int DIM>
-__device__ __forceinline__ double alpha_smoothed(const double* __restrict__ araw, unsigned e, const MeshArgs& ma) {
+__global__ void __launch_bounds__(256)
+k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, const MeshArgs ma) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ma.E) return;
   unsigned c[3] = {0, 0, 0};
-  elem_coords<DIM>(e, ma, c);
+  elem_coords<DIM>((unsigned)e, ma, c);
   double a = araw[e];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    a = fmax(a, 0.5 * araw[neighbour_of(e, c, d, +1, ma)]);
-    a = fmax(a, 0.5 * araw[neighbour_of(e, c, d, -1, ma)]);
+    a = fmax(a, 0.5 * araw[neighbour_of((unsigned)e, c, d, +1, ma)]);
+    a = fmax(a, 0.5 * araw[neighbour_of((unsigned)e, c, d, -1, ma)]);
   }
-  return a;
+  alpha[e] = a;
 }
 
 // u^n of node p of element e in the path's arithmetic
@@ -187,7 +192,7 @@ __device__ __forceinline__ R admissible_theta(const R* u0, const R* du, const Ph
 // ('-', its xi_d = 1 side) and ep ('+', its xi_d = 0 side).
 template <class EQ, int N, typename R>
 __device__ __forceinline__ void limited_face_flux(const double* __restrict__ uin, const R* __restrict__ trace,
-                                                  const double* __restrict__ araw, const MeshArgs& ma,
+                                                  const double* __restrict__ alpha, const MeshArgs& ma,
                                                   const PhysParams<R>& pp, const LimTab& lt, int d, unsigned em,
                                                   unsigned ep, int f, R dtR, R* F) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), C = trace_comps<EQ>();
@@ -210,7 +215,7 @@ __device__ __forceinline__ void limited_face_flux(const double* __restrict__ uin
   load_node<M, R>(uin, E, ep, NP, fb + stride, upi);
   R flo[M];
   rusanov_lo<EQ, R>(d, um, up, flo, pp);
-  const double af64 = 0.5 * (alpha_smoothed<DIM>(araw, em, ma) + alpha_smoothed<DIM>(araw, ep, ma));
+  const double af64 = 0.5 * (alpha[em] + alpha[ep]);
   const R af = dt_as<R>(af64);
   R Fb[M];
 #pragma unroll
@@ -241,13 +246,16 @@ __device__ __forceinline__ void limited_face_flux(const double* __restrict__ uin
 }
 
 // ---------------------------------------------------------------------------
-// Limited face / update kernel: one thread per node
+// Limited face / update kernel: one thread per node (alpha: the smoothed
+// coefficients; only_touched: leave the elements the limiter does not touch
+// to the lane kernel)
 // ---------------------------------------------------------------------------
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
-                      const R* __restrict__ trace, const double* __restrict__ araw, DevState* __restrict__ st,
-                      const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot) {
+                      const R* __restrict__ trace, const double* __restrict__ alpha, DevState* __restrict__ st,
+                      const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot,
+                      int only_touched) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), NF = NP / n;
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
@@ -255,13 +263,13 @@ k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout,
   const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
   R lam = R(0);
   bool bad = false;
-  if (gid < (unsigned)(E * NP)) {
-    const unsigned e = gid / NP;
+  const unsigned e = gid / NP;
+  if (gid < (unsigned)(E * NP) && !(only_touched && !limiter_touches<DIM>(alpha, e, ma))) {
     const int p = (int)(gid % NP);
     unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);
     const R dtR = step_dt<R>(st);
-    const double ae = alpha_smoothed<DIM>(araw, e, ma);
+    const double ae = alpha[e];
     R uc[M];
     load_node<M, R>(uin, E, e, NP, p, uc);
     // high-order increment (eq. crkfr.non.cons.final) and first-order subcell increment
@@ -292,7 +300,7 @@ k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout,
       }
       if (cd == N) {   // face xi_d = 1: this element is '-'
         R F[M];
-        limited_face_flux<EQ, N, R>(uin, trace, araw, ma, pp, lt, d, e, neighbour_of(e, ec, d, +1, ma), f, dtR, F);
+        limited_face_flux<EQ, N, R>(uin, trace, alpha, ma, pp, lt, d, e, neighbour_of(e, ec, d, +1, ma), f, dtR, F);
         const R s = dtR * tb.iwN * idx;
 #pragma unroll
         for (int v = 0; v < M; ++v) {
@@ -302,7 +310,7 @@ k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout,
       }
       if (cd == 0) {   // face xi_d = 0: this element is '+'
         R F[M];
-        limited_face_flux<EQ, N, R>(uin, trace, araw, ma, pp, lt, d, neighbour_of(e, ec, d, -1, ma), e, f, dtR, F);
+        limited_face_flux<EQ, N, R>(uin, trace, alpha, ma, pp, lt, d, neighbour_of(e, ec, d, -1, ma), e, f, dtR, F);
         const R s = dtR * tb.iw0 * idx;
 #pragma unroll
         for (int v = 0; v < M; ++v) {

@@ -828,13 +828,18 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
 // from the caller (dt_fused), slot is the CFL reduction's write slot itself,
 // and R-bar and the face records, written by other CTAs in the same launch,
 // are read through L2.
+// alpha != nullptr (subcell blending limiter): the elements the limiter
+// touches (blending coefficient of the element or of a face neighbour above
+// zero) are left out -- k_face_update_limited takes them -- and u^{n+1} of the
+// others goes to uout (the limited step keeps u^n intact).
 template <class EQ, int N, typename R, bool RK = false, bool FUSED = false>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
                                                 unsigned e0, int slot, R* __restrict__ sj,
                                                 const RkStage<R>& rk = RkStage<R>{nullptr, nullptr, 0, 1},
-                                                R dt_fused = R(0)) {
+                                                R dt_fused = R(0), const double* __restrict__ alpha = nullptr,
+                                                double* __restrict__ uout = nullptr) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
   constexpr bool F32 = sizeof(R) == 4;
@@ -845,8 +850,8 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   if constexpr (!FUSED) {
     if (st->status & ST_TIMEOUT) return;
   }
-  const bool active = (long long)e0 + el < E;
   const unsigned e = e0 + el;
+  const bool active = (long long)e0 + el < E && !(alpha && limiter_touches<DIM>(alpha, e, ma));
   const R dtR = FUSED ? dt_fused : step_dt<R>(st);
 
   // own x-line: Rbar and u^n (N+1 contiguous values per variable), loads issued first
@@ -958,7 +963,7 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
   // the CFL reduction of the new state (RKFR: after the last stage only; the
   // stage index is uniform over the grid); intermediate stage states go to
   // rk.uout
-  double* dst = u;
+  double* dst = uout ? uout : u;
   if (RK && rk.j != rk.s - 1) dst = rk.uout;
   else reduce_lambda<R>(lam, bad, st, FUSED ? slot : slot ^ 1);
   if (active) {
@@ -974,6 +979,18 @@ k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R*
                     int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   face_lanes_tile<EQ, N, R>(u, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot, reinterpret_cast<R*>(smem_raw));
+}
+
+// the limited step's elements that the limiter does not touch: the plain
+// update from u^n (uin) into uout (alpha: smoothed blending coefficients)
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
+k_face_update_lanes_clean(double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
+                          const R* __restrict__ trace, const double* __restrict__ alpha, DevState* __restrict__ st,
+                          const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, int slot) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  face_lanes_tile<EQ, N, R>(uin, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot, reinterpret_cast<R*>(smem_raw),
+                            RkStage<R>{nullptr, nullptr, 0, 1}, R(0), alpha, uout);
 }
 
 // face / update part of stage rk.j of the multi-stage RKFR step
