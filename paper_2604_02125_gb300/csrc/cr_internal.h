@@ -33,6 +33,7 @@ struct LaunchCtx {
   double* u_next;
   double* araw;
   double* alpha;      // smoothed coefficients
+  unsigned char* touched;   // 1 where the limited step changes the element's update
   LimTab lt;
   // fused single-launch step: per-tile readiness values
   unsigned* flags;

@@ -124,7 +124,7 @@ struct Variant {
     if constexpr (!EQ::NC) {
       const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
       k_alpha_raw<EQ, N><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
-      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.ma);
+      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.ma);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -137,7 +137,7 @@ struct Variant {
       if constexpr (kFaceLanes) {
         const unsigned tiles = (unsigned)((c.ma.E + 31) / 32);
         k_face_update_lanes_clean<EQ, N, R><<<tiles, FL::THREADS, FL::bytes(), s>>>(
-            c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.alpha, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c),
+            c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.touched, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c),
             c.slot);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -145,8 +145,8 @@ struct Variant {
       const long long total = c.ma.E * L::NP;
       const unsigned grid = (unsigned)((total + 255) / 256);
       k_face_update_limited<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.alpha,
-                                                           c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt, c.slot,
-                                                           kFaceLanes ? 1 : 0);
+                                                           c.touched, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt,
+                                                           c.slot, kFaceLanes ? 1 : 0);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;

@@ -249,23 +249,6 @@ __device__ __forceinline__ unsigned neighbour_of(unsigned e, const unsigned (&c)
   return c[d] == 0 ? e + (nd - 1) * stride : e - stride;
 }
 
-// Subcell blending limiter: whether the limited step changes element e's
-// update -- its own smoothed blending coefficient or a face neighbour's is
-// above zero (the face flux it shares is then blended).  Otherwise the
-// element's update is the plain cRKFR update.
-template <int DIM>
-__device__ __forceinline__ bool limiter_touches(const double* __restrict__ alpha, unsigned e, const MeshArgs& ma) {
-  unsigned c[3] = {0, 0, 0};
-  elem_coords<DIM>(e, ma, c);
-  double a = alpha[e];
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    a = fmax(a, alpha[neighbour_of(e, c, d, +1, ma)]);
-    a = fmax(a, alpha[neighbour_of(e, c, d, -1, ma)]);
-  }
-  return a > 0.0;
-}
-
 // ---------------------------------------------------------------------------
 // Volume kernel, tile form: one CTA holds epb elements; one thread per line.
 // Used where the lane form below does not fit in shared memory.

@@ -7,7 +7,9 @@
 //                        Legendre modes), the logistic map, its clips and the
 //                        cap alpha_max.  One thread per element.
 //  k_alpha_smooth        per element: a_e = max(raw_e, raw_nb / 2 over the
-//                        face neighbours).
+//                        face neighbours), and whether the limiter touches
+//                        the element (a_e or a face neighbour's a above zero,
+//                        i.e. a raw value above zero within two face steps).
 //  k_face_update_limited per node: the cRKFR update u^H with the limited face
 //                        flux at element faces, the first-order subcell update
 //                        u^L with the same face flux, the blend
@@ -111,21 +113,39 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
   araw[e] = fmin(a, lt.alpha_max);
 }
 
-// smoothed coefficient per element: max(raw_e, raw_nb / 2 over the face neighbours)
+// smoothed coefficient per element: max(raw_e, raw_nb / 2 over the face
+// neighbours); touched[e] = 1 where the limited step changes the element's
+// update: a raw coefficient above zero on the element, a face neighbour or a
+// face neighbour's face neighbour (the raw values are non-negative, so "above
+// zero" is "bits not all zero", tested with integer ORs)
 template <int DIM>
 __global__ void __launch_bounds__(256)
-k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, const MeshArgs ma) {
+k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, unsigned char* __restrict__ touched,
+               const MeshArgs ma) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ma.E) return;
+  const unsigned long long* rb = reinterpret_cast<const unsigned long long*>(araw);
   unsigned c[3] = {0, 0, 0};
   elem_coords<DIM>((unsigned)e, ma, c);
   double a = araw[e];
+  unsigned long long any = rb[e];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    a = fmax(a, 0.5 * araw[neighbour_of((unsigned)e, c, d, +1, ma)]);
-    a = fmax(a, 0.5 * araw[neighbour_of((unsigned)e, c, d, -1, ma)]);
-  }
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int off = -1; off <= 1; off += 2) {
+      const unsigned nb = neighbour_of((unsigned)e, c, d, off, ma);
+      a = fmax(a, 0.5 * araw[nb]);
+      unsigned cn[3] = {0, 0, 0};
+      elem_coords<DIM>(nb, ma, cn);
+      any |= rb[nb];
+#pragma unroll
+      for (int d2 = 0; d2 < DIM; ++d2) {
+        any |= rb[neighbour_of(nb, cn, d2, +1, ma)];
+        any |= rb[neighbour_of(nb, cn, d2, -1, ma)];
+      }
+    }
   alpha[e] = a;
+  touched[e] = any != 0ull ? 1 : 0;
 }
 
 // u^n of node p of element e in the path's arithmetic
@@ -253,9 +273,9 @@ __device__ __forceinline__ void limited_face_flux(const double* __restrict__ uin
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
-                      const R* __restrict__ trace, const double* __restrict__ alpha, DevState* __restrict__ st,
-                      const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot,
-                      int only_touched) {
+                      const R* __restrict__ trace, const double* __restrict__ alpha,
+                      const unsigned char* __restrict__ touched, DevState* __restrict__ st, const MeshArgs ma,
+                      const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot, int only_touched) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), NF = NP / n;
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
@@ -264,7 +284,7 @@ k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout,
   R lam = R(0);
   bool bad = false;
   const unsigned e = gid / NP;
-  if (gid < (unsigned)(E * NP) && !(only_touched && !limiter_touches<DIM>(alpha, e, ma))) {
+  if (gid < (unsigned)(E * NP) && !(only_touched && !touched[e])) {
     const int p = (int)(gid % NP);
     unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);

@@ -828,17 +828,18 @@ __device__ __forceinline__ void store_line(double* __restrict__ dst, const doubl
 // from the caller (dt_fused), slot is the CFL reduction's write slot itself,
 // and R-bar and the face records, written by other CTAs in the same launch,
 // are read through L2.
-// alpha != nullptr (subcell blending limiter): the elements the limiter
+// touched != nullptr (subcell blending limiter): the elements the limiter
 // touches (blending coefficient of the element or of a face neighbour above
-// zero) are left out -- k_face_update_limited takes them -- and u^{n+1} of the
-// others goes to uout (the limited step keeps u^n intact).
+// zero, flagged by k_alpha_smooth) are left out -- k_face_update_limited takes
+// them -- and u^{n+1} of the others goes to uout (the limited step keeps u^n
+// intact).
 template <class EQ, int N, typename R, bool RK = false, bool FUSED = false>
 __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R* __restrict__ rbar,
                                                 const R* __restrict__ trace, DevState* __restrict__ st,
                                                 const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
                                                 unsigned e0, int slot, R* __restrict__ sj,
                                                 const RkStage<R>& rk = RkStage<R>{nullptr, nullptr, 0, 1},
-                                                R dt_fused = R(0), const double* __restrict__ alpha = nullptr,
+                                                R dt_fused = R(0), const unsigned char* __restrict__ touched = nullptr,
                                                 double* __restrict__ uout = nullptr) {
   using L = FaceLaneLayout<EQ, N, R>;
   constexpr int DIM = L::DIM, M = L::M, n = L::n, NP = L::NP, NF = L::NF;
@@ -851,7 +852,7 @@ __device__ __forceinline__ void face_lanes_tile(double* __restrict__ u, const R*
     if (st->status & ST_TIMEOUT) return;
   }
   const unsigned e = e0 + el;
-  const bool active = (long long)e0 + el < E && !(alpha && limiter_touches<DIM>(alpha, e, ma));
+  const bool active = (long long)e0 + el < E && !(touched && touched[e]);
   const R dtR = FUSED ? dt_fused : step_dt<R>(st);
 
   // own x-line: Rbar and u^n (N+1 contiguous values per variable), loads issued first
@@ -982,15 +983,16 @@ k_face_update_lanes(double* __restrict__ u, const R* __restrict__ rbar, const R*
 }
 
 // the limited step's elements that the limiter does not touch: the plain
-// update from u^n (uin) into uout (alpha: smoothed blending coefficients)
+// update from u^n (uin) into uout (touched: the flags of k_alpha_smooth)
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(FaceLaneLayout<EQ, N, R>::THREADS)
 k_face_update_lanes_clean(double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
-                          const R* __restrict__ trace, const double* __restrict__ alpha, DevState* __restrict__ st,
-                          const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb, int slot) {
+                          const R* __restrict__ trace, const unsigned char* __restrict__ touched,
+                          DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                          int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   face_lanes_tile<EQ, N, R>(uin, rbar, trace, st, ma, pp, tb, blockIdx.x * 32u, slot, reinterpret_cast<R*>(smem_raw),
-                            RkStage<R>{nullptr, nullptr, 0, 1}, R(0), alpha, uout);
+                            RkStage<R>{nullptr, nullptr, 0, 1}, R(0), touched, uout);
 }
 
 // face / update part of stage rk.j of the multi-stage RKFR step

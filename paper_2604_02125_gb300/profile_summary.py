@@ -7,7 +7,8 @@ Two modes:
         --command "<the ncu command line>"
   per kernel, launch count, total device time and share of the total.
 
-  kernel capture (a `--set full -o X` run):
+  kernel capture (a `--set full -o X` run; X.ncu-rep, or the output of
+  `ncu -i X.ncu-rep --page raw --csv` saved as a .csv):
     python -m paper_2604_02125_gb300.profile_summary kernel X.ncu-rep --kernel REGEX --out profiles/NAME.md \
         --command "<the ncu command line>" --workload "<what ran>"
   duration, DRAM bytes, pipe utilisations, occupancy and stall reasons of
@@ -106,8 +107,14 @@ STALL = re.compile(r"smsp__average_warps_issue_stalled_(\w+)_per_issue_active\.r
 
 
 def kernel_rows(rep, kernel_regex):
-    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True,
-                         check=True).stdout
+    """Rows of the captured launches of a kernel: from an .ncu-rep (read with
+    `ncu -i REP --page raw --csv`) or from that command's saved output (.csv)."""
+    if rep.endswith(".csv"):
+        with open(rep) as f:
+            out = f.read()
+    else:
+        out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True,
+                             check=True).stdout
     rows = list(csv.reader(out.splitlines()))
     head, units = rows[0], rows[1]
     pat = re.compile(kernel_regex)
