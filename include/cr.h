@@ -137,6 +137,22 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  * element).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
+/* Caller-provided device memory.  cr_workspace_bytes stores in *bytes the
+ * device memory a single-solve context with this descriptor needs for its
+ * buffers (state, residual sums, face records, step record, totals, and what
+ * the scheme, limiter or the single-launch option adds), each 256-byte
+ * aligned; CR_EINVAL for an invalid descriptor.  No CUDA call.
+ * cr_init_mesh_ws is cr_init_mesh with n_solves = 1 whose device buffers are
+ * all carved out of `workspace` (a device pointer on the current device,
+ * 256-byte aligned, at least `bytes` >= cr_workspace_bytes long) instead of
+ * being allocated -- for callers whose own allocator (a framework's caching
+ * pool) already holds the device.  The caller keeps ownership and must keep
+ * the workspace alive and untouched until cr_destroy; CUDA graphs, streams and
+ * events of the context are still created by the library.  CR_EINVAL for a
+ * NULL, misaligned, too small, host or other-device workspace. */
+int cr_workspace_bytes(const cr_mesh_desc *desc, size_t *bytes);
+int cr_init_mesh_ws(cr_ctx **out, const cr_mesh_desc *desc, void *workspace, size_t bytes, void *cuda_stream);
+
 /* Number of conserved variables and of nodes (elements x (N+1)^dim) of a solve. */
 int cr_state_size(const cr_ctx *ctx, int solve, int *n_vars, long long *n_nodes);
 

@@ -42,7 +42,8 @@ _lib = None
 
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
            "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
-           "cr_probe_peak", "cr_tuning_info", "cr_check_conversions", "cr_set_state_async", "cr_get_state_async")
+           "cr_probe_peak", "cr_tuning_info", "cr_check_conversions", "cr_set_state_async", "cr_get_state_async",
+           "cr_workspace_bytes", "cr_init_mesh_ws")
 
 
 def load_library(path=None):
@@ -70,6 +71,8 @@ def load_library(path=None):
     lib.cr_probe_peak.argtypes = [ip, dp]
     lib.cr_tuning_info.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.cr_check_conversions.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.cr_workspace_bytes.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(ctypes.c_size_t)]
+    lib.cr_init_mesh_ws.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MeshDesc), vp, ctypes.c_size_t, vp]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -142,9 +145,12 @@ class Solver:
     default: each mesh dict's 'scheme' key, else 'crkfr'.
     stream: a cudaStream_t handle (int) or a torch.cuda.Stream; default: the
     current torch stream if torch has initialised CUDA, else the legacy stream.
+    workspace: a CUDA uint8 tensor of at least workspace_bytes(mesh, prec)
+    bytes (one mesh only): every device buffer of the context is carved out of
+    it (cr_init_mesh_ws); the solver keeps a reference to it.
     """
 
-    def __init__(self, mesh, prec="fp64", dt_fixed=0.0, stream=None, scheme=None):
+    def __init__(self, mesh, prec="fp64", dt_fixed=0.0, stream=None, scheme=None, workspace=None):
         self.lib = load_library()
         meshes = mesh if isinstance(mesh, (list, tuple)) else [mesh]
         self.meshes = list(meshes)
@@ -156,8 +162,16 @@ class Solver:
             stream = stream.cuda_stream
         self.stream = int(stream or 0)
         h = ctypes.c_void_p()
-        _check(self.lib.cr_init_mesh(ctypes.byref(h), arr, len(meshes), ctypes.c_void_p(self.stream)),
-               "cr_init_mesh")
+        if workspace is None:
+            _check(self.lib.cr_init_mesh(ctypes.byref(h), arr, len(meshes), ctypes.c_void_p(self.stream)),
+                   "cr_init_mesh")
+        else:
+            if len(meshes) != 1 or not getattr(workspace, "is_cuda", False) or not workspace.is_contiguous():
+                raise ValueError("workspace: one mesh and a contiguous CUDA tensor")
+            self._workspace = workspace
+            nbytes = workspace.numel() * workspace.element_size()
+            _check(self.lib.cr_init_mesh_ws(ctypes.byref(h), arr, ctypes.c_void_p(workspace.data_ptr()), nbytes,
+                                            ctypes.c_void_p(self.stream)), "cr_init_mesh_ws")
         self.h = h
 
     def state_size(self, solve=0):
@@ -287,6 +301,15 @@ def step_noalloc(mesh, u_in, u_out, dt_out=None, prec="fp64", dt_fixed=0.0, stre
                              ctypes.c_void_p(int(stream or 0)))
     _check(rc, "cr_step_noalloc")
     return rc
+
+
+def workspace_bytes(mesh, prec="fp64", scheme=None):
+    """Device bytes a single-solve context of this mesh needs (cr_workspace_bytes)."""
+    lib = load_library()
+    d = make_desc(mesh, prec, 0.0, scheme)
+    n = ctypes.c_size_t(0)
+    _check(lib.cr_workspace_bytes(ctypes.byref(d), ctypes.byref(n)), "cr_workspace_bytes")
+    return n.value
 
 
 PROBES = {"ffma": 0, "dfma": 1, "mufu_rcp": 2, "cvt_f64_f32": 3, "int_alu": 4, "copy_bytes": 5,

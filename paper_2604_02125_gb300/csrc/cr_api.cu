@@ -270,6 +270,8 @@ struct cr_ctx {
   // the volume kernel the FP32 one), joined before the face kernels
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // device buffers carved out of a caller's workspace (cr_init_mesh_ws): not freed here
+  bool borrowed = false;
   cudaStream_t cap_stream = nullptr;
   // the whole step in one cooperative launch (crkfr_fused.cuh), phases mod 3
   bool fused = false;
@@ -336,21 +338,30 @@ static void free_single(cr_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   c->side = nullptr;
   c->ev_fork = c->ev_join = nullptr;
-  cudaFree(c->ubuf[0]);
-  cudaFree(c->ubuf[1]);
+  if (!c->borrowed) {
+    cudaFree(c->ubuf[0]);
+    cudaFree(c->ubuf[1]);
+    cudaFree(c->lc.araw);
+    cudaFree(c->lc.alpha);
+    cudaFree(c->lc.touched);
+    cudaFree(c->lc.flags);
+    cudaFree(c->lc.rbar);
+    cudaFree(c->lc.trace);
+    cudaFree(c->lc.st);
+    cudaFree(c->lc.totals_part);
+    cudaFree(c->lc.ustage);
+    cudaFree(c->lc.kbuf);
+  }
   c->ubuf[0] = c->ubuf[1] = nullptr;
   c->lc.u = nullptr;
-  cudaFree(c->lc.araw);
-  cudaFree(c->lc.alpha);
-  cudaFree(c->lc.touched);
-  cudaFree(c->lc.flags);
+  c->lc.araw = c->lc.alpha = nullptr;
+  c->lc.touched = nullptr;
   c->lc.flags = nullptr;
-  cudaFree(c->lc.rbar);
-  cudaFree(c->lc.trace);
-  cudaFree(c->lc.st);
-  cudaFree(c->lc.totals_part);
-  cudaFree(c->lc.ustage);
-  cudaFree(c->lc.kbuf);
+  c->lc.rbar = c->lc.trace = nullptr;
+  c->lc.st = nullptr;
+  c->lc.totals_part = nullptr;
+  c->lc.ustage = nullptr;
+  c->lc.kbuf = nullptr;
   c->cap_stream = nullptr;
 }
 
@@ -419,7 +430,14 @@ static int capture(cr_ctx* c, int steps, int parity, cudaGraphExec_t* out) {
   return cuda_status(e);
 }
 
-static int init_single(cr_ctx* c) {
+// The device buffers of a single-solve context, in carving order: where each
+// pointer goes and its size.  Sets c->limited, c->fused and the sizes the
+// context keeps; no CUDA call.
+struct BufSpec {
+  void** p;
+  size_t bytes;
+};
+static int plan_single(cr_ctx* c, std::vector<BufSpec>* plan) {
   const cr_mesh_desc& d = c->desc[0];
   if (!get_ops(d.eq, d.dim, d.prec, d.vol, d.degree_N, &c->ops, d.ncflux)) return CR_EINVAL;
   const VariantOps& o = c->ops;
@@ -429,36 +447,12 @@ static int init_single(cr_ctx* c) {
   for (int k = 0; k < d.dim; ++k) E *= d.cells[k];
   c->E = E;
   LaunchCtx& lc = c->lc;
-  fill_launch_ctx(d, o, &lc);
   const long long nodes = E * o.NP;
   const long long NFt = E * o.NF;
   // one partial sum per CTA of the totals kernel (256 nodes per CTA)
   c->totals_blocks = (size_t)((nodes + 255) / 256);
-  int rc = CR_OK;
-  auto al = [&](void** p, size_t bytes) {
-    if (rc != CR_OK) return;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) rc = cuda_status(e);
-  };
   c->limited = d.limiter == CR_LIMITER_BLENDING;
   if (c->limited && (!o.alpha || !o.face_limited)) return CR_EINVAL;
-  al((void**)&c->ubuf[0], sizeof(double) * (size_t)o.M * nodes);
-  if (c->limited) {
-    al((void**)&c->ubuf[1], sizeof(double) * (size_t)o.M * nodes);
-    al((void**)&lc.araw, sizeof(double) * (size_t)E);
-    al((void**)&lc.alpha, sizeof(double) * (size_t)E);
-    al((void**)&lc.touched, (size_t)E);
-    fill_lim_tab(d.degree_N, d.alpha_max, &lc.lt);
-  }
-  lc.u = c->ubuf[0];
-  al(&lc.rbar, o.real_bytes * (size_t)o.M * nodes);
-  al(&lc.trace, o.real_bytes * ((size_t)o.dim * 2 * o.C * NFt + o.ncs_per_elem * (size_t)E));
-  al((void**)&lc.st, sizeof(DevState));
-  al((void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2));
-  if (d.scheme == CR_SCHEME_RKFR) {
-    al((void**)&lc.ustage, sizeof(double) * (size_t)o.M * nodes);
-    al(&lc.kbuf, o.real_bytes * (size_t)(rk_stages(d.degree_N) - 1) * o.M * nodes);
-  }
   // the single-launch step (crkfr_fused.cuh) on request only:
   // CRKFR_STEP_KERNELS=fused in the environment, for variants that have one.
   // Measured slower than the two kernels on every workload (the face / update
@@ -468,7 +462,58 @@ static int init_single(cr_ctx* c) {
   c->fused = o.step_fused && d.scheme == CR_SCHEME_CRKFR && d.ncflux == CR_NCFLUX_REDUCED && !c->limited && sk &&
              std::strcmp(sk, "fused") == 0;
   c->nphase = c->fused ? 3 : 2;
-  if (c->fused) al((void**)&lc.flags, sizeof(unsigned) * (size_t)((E + 31) / 32));
+  plan->clear();
+  plan->push_back({(void**)&c->ubuf[0], sizeof(double) * (size_t)o.M * nodes});
+  if (c->limited) {
+    plan->push_back({(void**)&c->ubuf[1], sizeof(double) * (size_t)o.M * nodes});
+    plan->push_back({(void**)&lc.araw, sizeof(double) * (size_t)E});
+    plan->push_back({(void**)&lc.alpha, sizeof(double) * (size_t)E});
+    plan->push_back({(void**)&lc.touched, (size_t)E});
+  }
+  plan->push_back({&lc.rbar, o.real_bytes * (size_t)o.M * nodes});
+  plan->push_back({&lc.trace, o.real_bytes * ((size_t)o.dim * 2 * o.C * NFt + o.ncs_per_elem * (size_t)E)});
+  plan->push_back({(void**)&lc.st, sizeof(DevState)});
+  plan->push_back({(void**)&lc.totals_part, sizeof(double) * c->totals_blocks * (o.M + 2)});
+  if (d.scheme == CR_SCHEME_RKFR) {
+    plan->push_back({(void**)&lc.ustage, sizeof(double) * (size_t)o.M * nodes});
+    plan->push_back({&lc.kbuf, o.real_bytes * (size_t)(rk_stages(d.degree_N) - 1) * o.M * nodes});
+  }
+  if (c->fused) plan->push_back({(void**)&lc.flags, sizeof(unsigned) * (size_t)((E + 31) / 32)});
+  return CR_OK;
+}
+
+static size_t align_ws(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t plan_bytes(const std::vector<BufSpec>& plan) {
+  size_t total = 0;
+  for (const BufSpec& b : plan) total += align_ws(b.bytes);
+  return total;
+}
+
+// workspace: nullptr = allocate every buffer; else carve them out of it
+// (ws_bytes checked against the plan by the caller)
+static int init_single(cr_ctx* c, void* workspace = nullptr) {
+  const cr_mesh_desc& d = c->desc[0];
+  std::vector<BufSpec> plan;
+  int rc = plan_single(c, &plan);
+  if (rc != CR_OK) return rc;
+  const VariantOps& o = c->ops;
+  const long long E = c->E;
+  LaunchCtx& lc = c->lc;
+  fill_launch_ctx(d, o, &lc);
+  if (c->limited) fill_lim_tab(d.degree_N, d.alpha_max, &lc.lt);
+  c->borrowed = workspace != nullptr;
+  size_t off = 0;
+  for (const BufSpec& b : plan) {
+    if (workspace) {
+      *b.p = static_cast<unsigned char*>(workspace) + off;
+      off += align_ws(b.bytes);
+    } else {
+      cudaError_t e = cudaMalloc(b.p, b.bytes);
+      if (e != cudaSuccess) { rc = cuda_status(e); break; }
+    }
+  }
+  lc.u = c->ubuf[0];
   if (rc != CR_OK) { free_single(c); return rc; }
   lc.ma.tma_ok = tma_ok_for(lc.u, E, o.NP);
   cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
@@ -517,6 +562,49 @@ int cr_init_mesh(cr_ctx** out, const cr_mesh_desc* desc, int n_solves, void* cud
   } else {
     rc = batched_init(&c->batched, c->desc.data(), n_solves, c->stream);
   }
+  if (rc != CR_OK) { delete c; return rc; }
+  *out = c;
+  return CR_OK;
+}
+
+int cr_workspace_bytes(const cr_mesh_desc* desc, size_t* bytes) {
+  if (!desc || !bytes || !desc_valid(*desc)) return CR_EINVAL;
+  cr_ctx tmp;
+  tmp.n_solves = 1;
+  tmp.desc.assign(desc, desc + 1);
+  std::vector<BufSpec> plan;
+  const int rc = plan_single(&tmp, &plan);
+  if (rc != CR_OK) return rc;
+  *bytes = plan_bytes(plan);
+  return CR_OK;
+}
+
+int cr_init_mesh_ws(cr_ctx** out, const cr_mesh_desc* desc, void* workspace, size_t bytes, void* cuda_stream) {
+  NvtxRange range("cr_init_mesh_ws");
+  if (!out) return CR_EINVAL;
+  *out = nullptr;
+  if (!desc || !workspace || (reinterpret_cast<size_t>(workspace) & 255) != 0 || !desc_valid(*desc)) return CR_EINVAL;
+  size_t need = 0;
+  int rc = cr_workspace_bytes(desc, &need);
+  if (rc != CR_OK) return rc;
+  if (bytes < need) return CR_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaPointerAttributes attr;
+  e = cudaPointerGetAttributes(&attr, workspace);
+  if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice || attr.device != dev) return CR_EINVAL;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (prop.major != 10 || prop.minor != 3) return CR_ENODEV;
+  cr_ctx* c = new (std::nothrow) cr_ctx();
+  if (!c) return CR_ENOMEM;
+  c->n_solves = 1;
+  c->desc.assign(desc, desc + 1);
+  c->stream = (cudaStream_t)cuda_stream;
+  c->device = dev;
+  rc = init_single(c, workspace);
   if (rc != CR_OK) { delete c; return rc; }
   *out = c;
   return CR_OK;

@@ -185,3 +185,37 @@ def test_random_descriptors_rejected_without_gpu(lib):
             [getattr(d, f) for f, _ in d._fields_ if f not in ("cells", "lo", "hi")])
         assert not h.value
     assert tried > 2500
+
+
+def test_workspace_bytes_without_gpu(lib):
+    """cr_workspace_bytes follows the documented buffer list (no CUDA call):
+    the state, R-bar, face records, step record and totals of the plain
+    step; a second state buffer and per-element coefficients with the limiter;
+    the stage state and s - 1 stage increments with the multi-stage scheme.
+    cr_init_mesh_ws rejects a NULL, misaligned or too small workspace before
+    any CUDA call."""
+    from paper_2604_02125_gb300 import crkfr, inputs
+    al = lambda b: (b + 255) // 256 * 256   # noqa: E731
+    mesh = inputs.mesh_dict("euler", 2, 3, [10, 7], [0, 0], [1.0, 1.0], 1.4)
+    E, NP, M, NF = 70, 16, 4, 4
+    nodes = E * NP
+    for prec, R in (("fp64", 8), ("fp32", 4)):
+        plain = (al(8 * M * nodes) + al(R * M * nodes) + al(R * 2 * 2 * (2 * M + 1) * NF * E) + al(64)
+                 + al(8 * ((nodes + 255) // 256) * (M + 2)))
+        assert crkfr.workspace_bytes(mesh, prec) == plain
+        lim = plain + al(8 * M * nodes) + al(8 * E) + al(8 * E) + al(E)
+        assert crkfr.workspace_bytes(dict(mesh, limiter=True), prec) == lim
+        rk = plain + al(8 * M * nodes) + al(R * 3 * M * nodes)
+        assert crkfr.workspace_bytes(mesh, prec, scheme="rkfr") == rk
+    n = ctypes.c_size_t()
+    bad = crkfr.make_desc(dict(mesh, N=7))
+    assert lib.cr_workspace_bytes(ctypes.byref(bad), ctypes.byref(n)) == crkfr.CR_EINVAL
+    d = crkfr.make_desc(mesh)
+    h = ctypes.c_void_p()
+    need = crkfr.workspace_bytes(mesh)
+    assert lib.cr_init_mesh_ws(ctypes.byref(h), ctypes.byref(d), None, need, None) == crkfr.CR_EINVAL
+    assert lib.cr_init_mesh_ws(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(4096 + 8), need, None) == \
+        crkfr.CR_EINVAL
+    assert lib.cr_init_mesh_ws(ctypes.byref(h), ctypes.byref(d), ctypes.c_void_p(4096), need - 1, None) == \
+        crkfr.CR_EINVAL
+    assert not h.value
