@@ -259,6 +259,13 @@ int cr_check_conversions(long long n, unsigned long long seed, long long *mismat
 int cr_step_noalloc(const cr_mesh_desc *desc, const double *u_in, double *u_out, double *dt_out,
                     void *cuda_stream);
 
+/* Subcell blending limiter: copy the smoothed blending coefficient of every
+ * element (E doubles, element order as in the state layout) that the last
+ * step used -- computed from the state it started from; zeros before the
+ * first step -- to a host (on_device = 0) or device pointer.  CR_EINVAL for a
+ * context without the limiter.  Synchronises the stream. */
+int cr_get_blend_alpha(cr_ctx *ctx, double *alpha, int on_device);
+
 /* JSON description of the kernel configuration chosen for the context (the
  * autotuned persistent grids of the batched form), copied into buf (len
  * bytes, NUL-terminated).  CR_EINVAL if it does not fit. */

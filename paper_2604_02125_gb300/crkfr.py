@@ -43,7 +43,7 @@ _lib = None
 EXPORTS = ("cr_init_mesh", "cr_state_size", "cr_set_state", "cr_step", "cr_sync", "cr_get_state",
            "cr_get_info", "cr_time_kernels", "cr_destroy", "cr_status_string", "cr_step_noalloc",
            "cr_probe_peak", "cr_tuning_info", "cr_check_conversions", "cr_set_state_async", "cr_get_state_async",
-           "cr_workspace_bytes", "cr_init_mesh_ws")
+           "cr_workspace_bytes", "cr_init_mesh_ws", "cr_get_blend_alpha")
 
 
 def load_library(path=None):
@@ -73,6 +73,7 @@ def load_library(path=None):
     lib.cr_check_conversions.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]
     lib.cr_workspace_bytes.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(ctypes.c_size_t)]
     lib.cr_init_mesh_ws.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MeshDesc), vp, ctypes.c_size_t, vp]
+    lib.cr_get_blend_alpha.argtypes = [vp, dp, ip]
     lib.cr_status_string.argtypes = [ip]
     lib.cr_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -238,6 +239,15 @@ class Solver:
         nb = flush.numel() * flush.element_size() if flush is not None else 0
         _check(self.lib.cr_time_kernels(self.h, int(nsteps), fp, nb, ms), "cr_time_kernels")
         return ms[0], ms[1]
+
+    def blend_alpha(self):
+        """Smoothed blending coefficients of the elements that the last step
+        used (subcell blending limiter; cr_get_blend_alpha)."""
+        from . import inputs
+        out = np.zeros(inputs.num_elems(self.meshes[0]))
+        _check(self.lib.cr_get_blend_alpha(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0),
+               "cr_get_blend_alpha")
+        return out
 
     def tuning_info(self):
         """The kernel configuration chosen for this context (JSON)."""

@@ -189,6 +189,14 @@ void fill_lim_tab(int N, double alpha_max, LimTab* lt) {
   lt->tau = 0.5 * std::pow(10.0, -1.8 * std::pow(N + 1.0, 0.25));
   lt->sharp = std::log(9999.0);
   lt->alpha_max = alpha_max;
+  for (int j = 0; j < 6; ++j)
+    for (int p = 0; p < 6; ++p) lt->vinv_f[j][p] = (float)lt->vinv[j][p];
+  lt->tau_f = (float)lt->tau;
+  lt->sharp_f = (float)lt->sharp;
+  lt->alpha_max_f = (float)alpha_max;
+  // the energy fractions where 1/(1 + exp(-(sharp/tau)(E - tau))) = 0.001 and 0.999
+  lt->e_lo_f = (float)(lt->tau * (1.0 + std::log(0.001 / 0.999) / lt->sharp));
+  lt->e_hi_f = (float)(lt->tau * (1.0 + std::log(0.999 / 0.001) / lt->sharp));
 }
 
 void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* plc) {
@@ -519,6 +527,7 @@ static int init_single(cr_ctx* c, void* workspace = nullptr) {
   cudaError_t e = o.set_smem(o.vol_smem(lc.epb));
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   e = cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream);
+  if (e == cudaSuccess && c->limited) e = cudaMemsetAsync(lc.alpha, 0, sizeof(double) * (size_t)E, c->stream);
   if (e == cudaSuccess && c->fused) e = cudaMemsetAsync(lc.flags, 0, sizeof(unsigned) * (size_t)((E + 31) / 32), c->stream);
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -798,6 +807,14 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
   ms[0] = tv / nsteps;
   ms[1] = c->fused ? 0.0 : tf / nsteps;
   return read_status(c);
+}
+
+int cr_get_blend_alpha(cr_ctx* c, double* alpha, int on_device) {
+  if (!c || !alpha || c->batched || !c->limited) return CR_EINVAL;
+  CR_TRY(cudaMemcpyAsync(alpha, c->lc.alpha, sizeof(double) * (size_t)c->E,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CR_TRY(cudaStreamSynchronize(c->stream));
+  return CR_OK;
 }
 
 int cr_destroy(cr_ctx* c) {

@@ -123,7 +123,7 @@ struct Variant {
   static cudaError_t alpha(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (!EQ::NC) {
       const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
-      k_alpha_raw<EQ, N><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
+      k_alpha_raw<EQ, N, R><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
       k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.ma);
       return cudaGetLastError();
     }

@@ -131,7 +131,9 @@ __device__ __forceinline__ void reduce_lambda(T lam, bool bad, DevState* st, int
   const unsigned anybad = __ballot_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
     if (anybad) atomicOr(&st->status, ST_NONPHYS);
-    atomicMax(&st->lam_bits[slot], (unsigned long long)__double_as_longlong((double)lam));
+    // a warp whose lanes did no work (maximum 0) leaves the slot alone: the
+    // atomics of thousands of idle warps on one word would serialise
+    if (lam > T(0)) atomicMax(&st->lam_bits[slot], (unsigned long long)__double_as_longlong((double)lam));
   }
 }
 

@@ -2,10 +2,12 @@
 // paper's Sec. 4 runs blend the update with a first-order subcell finite-volume
 // update, the blending coefficient capped by alpha_max; compressible Euler).
 //
-//  k_alpha_raw           per element, FP64: the modal smoothness indicator of
-//                        rho p (energy fraction of the highest orthonormal
-//                        Legendre modes), the logistic map, its clips and the
-//                        cap alpha_max.  One thread per element.
+//  k_alpha_raw           per element: the modal smoothness indicator of rho p
+//                        (energy fraction of the highest orthonormal Legendre
+//                        modes), the logistic map, its clips and the cap
+//                        alpha_max; FP64, or in the FP32 form FP32 with the
+//                        FP64 evaluation near the clip thresholds.  One thread
+//                        per element.
 //  k_alpha_smooth        per element: a_e = max(raw_e, raw_nb / 2 over the
 //                        face neighbours), and whether the limiter touches
 //                        the element (a_e or a face neighbour's a above zero,
@@ -38,51 +40,64 @@
 
 namespace crk {
 
-// Host-filled tables of the limiter (FP64).
+// Host-filled tables of the limiter.
 struct LimTab {
   double vinv[6][6];   // orthonormal Legendre modes from GLL node values: m_j = sum_p vinv[j][p] v_p
   double w01[6];       // GLL weights on [0,1] (subcell widths / dx)
   double tau, sharp;   // logistic threshold 0.5 10^(-1.8 (N+1)^(1/4)) and sharpness ln 9999
   double alpha_max;
+  // FP32 form: the same tables in FP32, and the energy fractions at which the
+  // logistic map crosses the clips (alpha = 0.001: tau (1 + ln(0.001/0.999)/sharp),
+  // alpha = 0.999: tau (1 + ln(0.999/0.001)/sharp))
+  float vinv_f[6][6];
+  float tau_f, sharp_f, alpha_max_f, e_lo_f, e_hi_f;
 };
 
-// ---------------------------------------------------------------------------
-// Blending coefficient per element before smoothing
-// ---------------------------------------------------------------------------
-template <class EQ, int N>
-__global__ void __launch_bounds__(128)
-k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshArgs ma, const LimTab lt) {
+// Energy fraction of the highest modes of one element's rho p (see
+// k_alpha_raw).  FP64: E = max((T - T1)/T, (T1 - T2)/T1) from the three sums;
+// FP32: the top and second-top energies summed directly (sums of squares, no
+// cancellation), E = max(Ttop/T, Tsec/(T - Ttop)).
+template <class EQ, int N, typename T>
+__device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long long E, long long e,
+                                              const MeshArgs& ma, const LimTab& lt) {
   constexpr int DIM = EQ::DIM, n = N + 1, NP = ipow(n, DIM);
-  const long long E = ma.E;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  double m[NP];
+  constexpr bool F32 = sizeof(T) == 4;
+  T m[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const double rho = u[(size_t)e * NP + p];
-    double mm = 0.0;
+    T rho, Et, mm = T(0);
+    if constexpr (F32) {
+      rho = d2f_int(u[(size_t)e * NP + p]);
+      Et = d2f_int(u[((size_t)(DIM + 1) * E + e) * NP + p]);
+    } else {
+      rho = u[(size_t)e * NP + p];
+      Et = u[((size_t)(DIM + 1) * E + e) * NP + p];
+    }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      const double mk = u[((size_t)(1 + k) * E + e) * NP + p];
+      T mk;
+      if constexpr (F32) mk = d2f_int(u[((size_t)(1 + k) * E + e) * NP + p]);
+      else mk = u[((size_t)(1 + k) * E + e) * NP + p];
       mm += mk * mk;
     }
-    const double Et = u[((size_t)(DIM + 1) * E + e) * NP + p];
     // rho p = (gamma - 1)(rho E - |m|^2 / 2)
-    m[p] = (ma.gamma - 1.0) * (rho * Et - 0.5 * mm);
+    const T gm1 = F32 ? T(ma.gamma_f - 1.0f) : T(ma.gamma - 1.0);
+    m[p] = gm1 * (rho * Et - T(0.5) * mm);
   }
-  // modal coefficients: the 1D transform along every direction in turn
+  // modal coefficients: the 1D transform along every direction in turn (fully
+  // unrolled: compile-time indices keep the element's values in registers)
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int stride = ipow(n, d);
-#pragma unroll 1
+#pragma unroll
     for (int l = 0; l < NP / n; ++l) {
       const int base = line_base<n>(l, stride);
-      double t[n];
+      T t[n];
 #pragma unroll
       for (int j = 0; j < n; ++j) {
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
-        for (int p = 0; p < n; ++p) acc += lt.vinv[j][p] * m[base + p * stride];
+        for (int p = 0; p < n; ++p) acc += (F32 ? T(lt.vinv_f[j][p]) : T(lt.vinv[j][p])) * m[base + p * stride];
         t[j] = acc;
       }
 #pragma unroll
@@ -90,7 +105,8 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
     }
   }
   // energy of all modes, of those of degree <= N-1 and <= N-2 in every direction
-  double T = 0.0, T1 = 0.0, T2 = 0.0;
+  // (FP32: of those of degree N and N-1 at most, summed directly)
+  T tot = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     int rem = p, top = 0;
@@ -100,13 +116,52 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
       rem /= n;
       top = j > top ? j : top;
     }
-    const double e2 = m[p] * m[p];
-    T += e2;
-    if (top <= N - 1) T1 += e2;
-    if (top <= N - 2) T2 += e2;
+    const T e2 = m[p] * m[p];
+    tot += e2;
+    if constexpr (F32) {
+      if (top == N) a1 += e2;
+      if (top == N - 1) a2 += e2;
+    } else {
+      if (top <= N - 1) a1 += e2;
+      if (top <= N - 2) a2 += e2;
+    }
   }
-  double En = (T - T1) / T;
-  if (N >= 2) En = fmax(En, (T1 - T2) / T1);
+  T En;
+  if constexpr (F32) {
+    En = a1 / tot;
+    if (N >= 2) En = fmax(En, a2 / (tot - a1));
+  } else {
+    En = (tot - a1) / tot;
+    if (N >= 2) En = fmax(En, (a1 - a2) / a1);
+  }
+  return En;
+}
+
+// ---------------------------------------------------------------------------
+// Blending coefficient per element before smoothing.  The FP64 form evaluates
+// it in FP64 throughout.  The FP32 form evaluates the energy fraction in FP32
+// and takes the FP64 evaluation for the elements whose FP32 value lies within
+// 2% of a clip threshold, so every clip decision is the FP64 one (the FP32
+// value's relative error is below 1e-4 there); elsewhere the logistic map in
+// FP32 differs from the FP64 one by about 1e-6.
+// ---------------------------------------------------------------------------
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(128)
+k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshArgs ma, const LimTab lt) {
+  const long long E = ma.E;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  if constexpr (sizeof(R) == 4) {
+    const float En = indicator_energy<EQ, N, float>(u, E, e, ma, lt);
+    const bool near = fabsf(En - lt.e_lo_f) <= 0.02f * lt.e_lo_f || fabsf(En - lt.e_hi_f) <= 0.02f * lt.e_hi_f;
+    if (!near) {
+      float a = En < lt.e_lo_f ? 0.0f : En > lt.e_hi_f ? 1.0f
+                                       : 1.0f / (1.0f + expf(-(lt.sharp_f / lt.tau_f) * (En - lt.tau_f)));
+      araw[e] = f2d_int(fminf(a, lt.alpha_max_f));
+      return;
+    }
+  }
+  const double En = indicator_energy<EQ, N, double>(u, E, e, ma, lt);
   double a = 1.0 / (1.0 + exp(-(lt.sharp / lt.tau) * (En - lt.tau)));
   if (a < 0.001) a = 0.0;
   if (a > 0.999) a = 1.0;

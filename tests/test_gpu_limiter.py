@@ -16,7 +16,10 @@ coefficient capped by alpha_max).
   1000) every element takes alpha = 1 and the step is the first-order one,
   which stays positive under the first-order time step bound;
 * the 256^2 shear layer at N = 3 with the KEP flux and alpha_max = 0.008 (the
-  paper's Kelvin-Helmholtz setting), one step on every node.
+  paper's Kelvin-Helmholtz setting), one step on every node;
+* the coefficients a step used (cr_get_blend_alpha) against the oracle's:
+  the same elements at zero, at the cap and in between, FP64 to 1e-12 and
+  FP32 (energy fractions in FP32, FP64 near the clip thresholds) to 1e-5.
 """
 import numpy as np
 import pytest
@@ -189,3 +192,27 @@ def test_full_size_256(cr, orc, prec, case):
     O = orc.step(mesh, U, info["dt"])
     check_close(G, O, STATE_TOL[prec])
     check_increment(G, O, U, INC_TOL[prec])
+
+
+@pytest.mark.parametrize("dim,N", [(1, 2), (1, 5), (2, 1), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_blend_coefficients_match_oracle(cr, orc, dim, N, prec):
+    mesh, U = fronts_state(dim, N, "ec", seed=700 + 10 * dim + N)
+    _, ref = orc.blend_alpha(mesh, U)
+    with cr.Solver(mesh, prec=prec) as s:
+        s.set_state(U)
+        assert np.all(s.blend_alpha() == 0.0)      # before the first step
+        s.step(1)
+        a = s.blend_alpha()
+    am = mesh["alpha_max"]
+    assert np.array_equal(a == 0.0, ref == 0.0)
+    assert np.array_equal(a == am, ref == am) or prec == "fp32"
+    assert np.max(np.abs(a - ref)) <= (1e-12 if prec == "fp64" else 1e-5), np.max(np.abs(a - ref))
+    assert np.any(ref > 0.0)
+
+
+def test_blend_alpha_needs_the_limiter(cr):
+    mesh, U = inputs.shear_layer_2d(cells=(8, 8), N=3)
+    with cr.Solver(mesh) as s:
+        with pytest.raises(cr.CrError):
+            s.blend_alpha()
