@@ -92,8 +92,12 @@ struct RefTab {
 // rotates read / write / clear slots modulo 3, because its clear and its
 // reductions happen within one launch.  epoch[] carries its per-step tile
 // readiness value the same way.
+// Each slot is spread over kLamSpread words: warp w of CTA b reduces into word
+// (b NW + w) mod kLamSpread, and the step start takes the maximum of the
+// words -- thousands of warps' atomics on a single word would serialise.
+constexpr int kLamSpread = 32;
 struct DevState {
-  unsigned long long lam_bits[3];   // max over nodes of sum_d lambda_d / dx_d (bits of a non-negative double)
+  unsigned long long lam_bits[3][kLamSpread];   // max over nodes of sum_d lambda_d / dx_d (bits of a non-negative double)
   unsigned epoch[3];   // fused step: readiness value of the step that starts from a slot
   unsigned pad0;
   double dt;           // dt of the last step (set when the step starts)
@@ -121,7 +125,7 @@ struct RkStage {
 
 // ---------------------------------------------------------------------------
 // CFL reduction: every warp takes its maximum with shuffles and folds it into
-// lam_bits[slot] with one 64-bit atomicMax (non-negative doubles order like
+// its word of lam_bits[slot] with one 64-bit atomicMax (non-negative doubles order like
 // their bit patterns; the result is not waited for).  Must be reached by every
 // lane of the warp.
 // ---------------------------------------------------------------------------
@@ -133,7 +137,10 @@ __device__ __forceinline__ void reduce_lambda(T lam, bool bad, DevState* st, int
     if (anybad) atomicOr(&st->status, ST_NONPHYS);
     // a warp whose lanes did no work (maximum 0) leaves the slot alone: the
     // atomics of thousands of idle warps on one word would serialise
-    if (lam > T(0)) atomicMax(&st->lam_bits[slot], (unsigned long long)__double_as_longlong((double)lam));
+    if (lam > T(0)) {
+      const unsigned word = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kLamSpread;
+      atomicMax(&st->lam_bits[slot][word], (unsigned long long)__double_as_longlong((double)lam));
+    }
   }
 }
 
@@ -143,10 +150,18 @@ __device__ __forceinline__ void reduce_lambda(T lam, bool bad, DevState* st, int
 // records the step and clears the other slot for the new state's reduction.
 __device__ __forceinline__ double step_begin_slots(DevState* st, int slot, int clear_slot, double cfl, double dt_fixed,
                                                    bool lead) {
-  const double lam = __longlong_as_double((long long)st->lam_bits[slot]);
+  // all words loaded at once (one round trip), then reduced
+  unsigned long long w[kLamSpread];
+#pragma unroll
+  for (int k = 0; k < kLamSpread; ++k) w[k] = st->lam_bits[slot][k];
+  unsigned long long bits = 0ull;
+#pragma unroll
+  for (int k = 0; k < kLamSpread; ++k) bits = max(bits, w[k]);
+  const double lam = __longlong_as_double((long long)bits);
   const double dt = dt_fixed > 0.0 ? dt_fixed : cfl / lam;
   if (lead) {
-    st->lam_bits[clear_slot] = 0ull;
+#pragma unroll 8
+    for (int k = 0; k < kLamSpread; ++k) st->lam_bits[clear_slot][k] = 0ull;
     st->dt = dt;
     st->t += dt;
     st->steps += 1;
@@ -158,6 +173,7 @@ __device__ __forceinline__ double step_begin_slots(DevState* st, int slot, int c
 __device__ __forceinline__ double step_begin(DevState* st, int slot, double cfl, double dt_fixed, bool lead) {
   return step_begin_slots(st, slot, slot ^ 1, cfl, dt_fixed, lead);
 }
+
 
 // Loads of data another CTA wrote earlier in the same launch (fused step):
 // through L2 (ld.global.cg), never the non-coherent path or a stale L1 line.
