@@ -52,14 +52,13 @@ __device__ __forceinline__ f2& operator*=(f2& a, f2 b) { return a = f2(a * b); }
 __device__ __forceinline__ f2 fast_rcp(f2 x) { return f2(fast_rcp(x.v.x), fast_rcp(x.v.y)); }
 
 __device__ __forceinline__ f2 series_F(f2 u) {
-  const f2 c11(1.0f / 11.0f), c9(1.0f / 9.0f), c7(1.0f / 7.0f), c5(1.0f / 5.0f), c3(1.0f / 3.0f), c1(1.0f);
-  return u * (u * (u * (u * (u * c11 + c9) + c7) + c5) + c3) + c1;
+  const f2 c9(1.0f / 9.0f), c7(1.0f / 7.0f), c5(1.0f / 5.0f), c3(1.0f / 3.0f), c1(1.0f);
+  return u * (u * (u * (u * c9 + c7) + c5) + c3) + c1;
 }
 
 __device__ __forceinline__ f2 series_invF(f2 u) {
-  const f2 c5(-10196.0f / 467775.0f), c4(-428.0f / 14175.0f), c3(-44.0f / 945.0f), c2(-4.0f / 45.0f),
-      c1(-1.0f / 3.0f), c0(1.0f);
-  return u * (u * (u * (u * (u * c5 + c4) + c3) + c2) + c1) + c0;
+  const f2 c4(-428.0f / 14175.0f), c3(-44.0f / 945.0f), c2(-4.0f / 45.0f), c1(-1.0f / 3.0f), c0(1.0f);
+  return u * (u * (u * (u * c4 + c3) + c2) + c1) + c0;
 }
 
 // L(a1,b1) and 1/L(a2,b2) in both halves, as the scalar FP32 version: one

@@ -31,14 +31,15 @@ struct PhysParams {
 // For a ~ b both use the series in u = ((a-b)/(a+b))^2:
 //   L = (a+b) / (2 F(u)),  F(u) = 1 + u/3 + u^2/5 + u^3/7 + ...
 // FP64: 4 terms below u = 1e-4 (truncation u^4/9 < 1.2e-17).
-// FP32: 6 terms below u = 0.05 (truncation u^6/13 < 1.2e-9); above it the
-// ratio a/b exceeds 1.57 and log(a/b) is well conditioned.
+// FP32: 5 terms below u = 0.05 (truncation below u^5 / (11 (1 - u)) < 3e-8,
+// half an FP32 ulp of F ~ 1); above it the ratio a/b exceeds 1.57 and
+// log(a/b) is well conditioned.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double series_F(double u) {
   return 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
 }
 __device__ __forceinline__ float series_F(float u) {
-  return 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f + u * (1.0f / 9.0f + u * (1.0f / 11.0f)))));
+  return 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f + u * (1.0f / 9.0f))));
 }
 template <typename R> struct LogMeanEps;
 template <> struct LogMeanEps<double> { static constexpr double v = 1e-4; };
@@ -100,12 +101,11 @@ __device__ __forceinline__ void logmean_pair(R a1, R b1, R a2, R b2, R& L1, R& i
   }
 }
 
-// FP32: 1/F(u) = sqrt(u)/artanh(sqrt(u)) by its own series (six terms; the
-// truncation is below 3e-10 relative for u < 0.05), so that the series branch
+// FP32: 1/F(u) = sqrt(u)/artanh(sqrt(u)) by its own series (five terms; the
+// truncation is below 7e-9 relative for u < 0.05), so that the series branch
 // needs a single reciprocal: 1/(s1 s2) gives both 1/s1 and 1/s2.
 __device__ __forceinline__ float series_invF(float u) {
-  return 1.0f + u * (-1.0f / 3.0f + u * (-4.0f / 45.0f + u * (-44.0f / 945.0f + u * (-428.0f / 14175.0f
-             + u * (-10196.0f / 467775.0f)))));
+  return 1.0f + u * (-1.0f / 3.0f + u * (-4.0f / 45.0f + u * (-44.0f / 945.0f + u * (-428.0f / 14175.0f))));
 }
 __device__ __forceinline__ void logmean_pair(float a1, float b1, float a2, float b2, float& L1, float& iL2) {
   const float s1 = a1 + b1, d1 = a1 - b1, s2 = a2 + b2, d2 = a2 - b2;

@@ -408,7 +408,9 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   const PhysParams<f2> pp2{f2(float(pp.gamma)), f2(float(pp.inv_gm1)), f2(float(pp.c_h)), pp.vol};
 
   // ---- u^n: coalesced into shared memory (staging in the Q region), then own x-line to registers
-  // (index arithmetic with compile-time divisors only)
+  // (index arithmetic with compile-time divisors only).  FP32 form: the hardware conversion, one
+  // issue slot on the FP64 pipe, which this kernel leaves otherwise idle (the integer d2f_int is
+  // about twenty ALU instructions; measured 59.5 -> 56.6 us per launch, 2D Euler 256^2, N = 3)
 #pragma unroll 4
   for (int it = 0; it < (M * 32 * NP + L::THREADS - 1) / L::THREADS; ++it) {
     const int idx = tid + it * L::THREADS;
@@ -416,7 +418,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     const int ee = r / NP, p = r % NP;
     if (v < M && ee < nel) {
       const double x = staged ? staged[(size_t)v * 32 * NP + r] : u[((size_t)v * E + e0) * NP + r];
-      if constexpr (sizeof(R) == 4) sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = d2f_int(x);
+      if constexpr (sizeof(R) == 4) sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = __double2float_rn(x);
       else sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = x;
     }
   }

@@ -200,7 +200,10 @@ def test_workspace_bytes_without_gpu(lib):
     E, NP, M, NF = 70, 16, 4, 4
     nodes = E * NP
     for prec, R in (("fp64", 8), ("fp32", 4)):
-        plain = (al(8 * M * nodes) + al(R * M * nodes) + al(R * 2 * 2 * (2 * M + 1) * NF * E) + al(64)
+        # the step record: three CFL slots of 32 64-bit words, three epochs and
+        # a pad word, dt, t, the wave-speed maximum, the step count, status, pad
+        step_record = 3 * 32 * 8 + 4 * 4 + 3 * 8 + 8 + 2 * 4
+        plain = (al(8 * M * nodes) + al(R * M * nodes) + al(R * 2 * 2 * (2 * M + 1) * NF * E) + al(step_record)
                  + al(8 * ((nodes + 255) // 256) * (M + 2)))
         assert crkfr.workspace_bytes(mesh, prec) == plain
         lim = plain + al(8 * M * nodes) + al(8 * E) + al(8 * E) + al(E)
