@@ -280,6 +280,33 @@ struct LaneLayout<EQ, N, R, 1> : LaneLayout<EQ, N, R, 0> {
   static constexpr int MINB = B::PACK ? B::MINB + 1 : (B::MINB > 1 ? B::MINB - 1 : 1);
 };
 
+// face_accumulate for both lines of the packed form at once (x-line ends in
+// the low halves, y-line ends in the high halves, the latter in the frame of
+// the y-line); the wave speeds are taken separately
+template <class EQ, int N>
+__device__ __forceinline__ void face_accumulate_xy(FaceAcc<EQ, f2>& fa, const f2 (&q)[N + 1][EQ::P],
+                                                   const f2 (&fend)[2][EQ::M], f2 b, bool first,
+                                                   const PhysParams<f2>& pp) {
+  constexpr int M = EQ::M;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    f2 uu[M];
+    EQ::cons_from_pair(q[side ? N : 0], uu, pp);
+    if (first) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        fa.U[side][v] = f2(0.0f);
+        fa.F[side][v] = f2(0.0f);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      fa.U[side][v] += b * uu[v];
+      fa.F[side][v] += b * fend[side][v];
+    }
+  }
+}
+
 template <class EQ, int N, typename R, int D>
 __device__ __forceinline__ void face_accumulate(FaceAcc<EQ, R>& fa, const R (&q)[N + 1][EQ::P],
                                                 const R (&fend)[2][EQ::M], R b, bool first,
@@ -411,15 +438,30 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
   // (index arithmetic with compile-time divisors only).  FP32 form: the hardware conversion, one
   // issue slot on the FP64 pipe, which this kernel leaves otherwise idle (the integer d2f_int is
   // about twenty ALU instructions; measured 59.5 -> 56.6 us per launch, 2D Euler 256^2, N = 3)
-#pragma unroll 4
-  for (int it = 0; it < (M * 32 * NP + L::THREADS - 1) / L::THREADS; ++it) {
-    const int idx = tid + it * L::THREADS;
-    const int v = idx / (32 * NP), r = idx % (32 * NP);
-    const int ee = r / NP, p = r % NP;
-    if (v < M && ee < nel) {
-      const double x = staged ? staged[(size_t)v * 32 * NP + r] : u[((size_t)v * E + e0) * NP + r];
-      if constexpr (sizeof(R) == 4) sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = __double2float_rn(x);
-      else sm[(size_t)ee * L::SZ + L::O_U0 + v * NP + p] = x;
+  // each variable's 32 NP values are n rounds of the CTA's 32 NF threads:
+  // the node offsets of the rounds are computed once, the variable loop only
+  // adds its stride
+  static_assert(32 * NP == n * L::THREADS, "a tile's values per variable are n rounds of the CTA");
+  int tofs[n];
+  bool tok[n];
+#pragma unroll
+  for (int j = 0; j < n; ++j) {
+    const int r = tid + j * L::THREADS, ee = r / NP;
+    tofs[j] = ee * L::SZ + L::O_U0 + r % NP;
+    tok[j] = ee < nel;
+  }
+  {
+    const double* src = staged ? staged + tid : u + (size_t)e0 * NP + tid;
+    const size_t vstride = staged ? (size_t)32 * NP : (size_t)E * NP;
+#pragma unroll 1
+    for (int v = 0; v < M; ++v, src += vstride) {
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+        if (tok[j]) {
+          const double x = src[j * L::THREADS];
+          if constexpr (sizeof(R) == 4) sm[tofs[j] + v * NP] = __double2float_rn(x);
+          else sm[tofs[j] + v * NP] = x;
+        }
     }
   }
   __syncthreads();
@@ -433,6 +475,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     for (int v = 0; v < M; ++v) { rb[k][v] = R(0); ax[k][v] = R(0); }
   // face sums of the ends of this thread's x-line (faces normal to x), y-line and z-line
   FaceAcc<EQ, R> fx, fy, fz;
+  FaceAcc<EQ, f2> fxy;   // packed form: both lines' face sums
 
   // the stage loop stays rolled: one stage's code is large, and S copies of it
   // would overflow the instruction cache; the tableau comes from the parameters
@@ -508,14 +551,6 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
 #pragma unroll
           for (int c = 0; c < P; ++c) q2[k][c] = f2(q[k][c], qy[k][PackXY<EQ>::rot(c)]);
         line_residual_xy<EQ, N>(q2, acc2, fe2, pp2, tb, f2(inv_dx_of<float>(ma, 0), inv_dx_of<float>(ma, 1)));
-        R fex[2][M], fey[2][M];
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd)
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            fex[sd][v] = fe2[sd][v].v.x;
-            fey[sd][v] = fe2[sd][PackXY<EQ>::rot(v)].v.y;
-          }
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -523,8 +558,14 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
             ax[k][v] = acc2[k][v].v.x;
             my[L::O_RY + v * NP + l + k * n] = acc2[k][PackXY<EQ>::rot(v)].v.y;
           }
-        face_accumulate<EQ, N, R, 0>(fx, q, fex, bi, i == 0, pp);
-        face_accumulate<EQ, N, R, 1>(fy, qy, fey, bi, i == 0, pp);
+        if (i == 0) {
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            fx.lam[sd] = EQ::wave_speed(0, q[sd ? N : 0], pp);
+            fy.lam[sd] = EQ::wave_speed(1, qy[sd ? N : 0], pp);
+          }
+        }
+        face_accumulate_xy<EQ, N>(fxy, q2, fe2, f2(bi), i == 0, pp2);
       }
       __syncthreads();   // RY complete
     } else if constexpr (ROLLP) {
@@ -629,12 +670,22 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     }
   }
   __syncthreads();
-#pragma unroll 4
-  for (int it = 0; it < (M * 32 * NP + L::THREADS - 1) / L::THREADS; ++it) {
-    const int idx = tid + it * L::THREADS;
-    const int v = idx / (32 * NP), r = idx % (32 * NP);
-    const int ee = r / NP, p = r % NP;
-    if (v < M && ee < nel) rbar[((size_t)v * E + e0) * NP + r] = sm[(size_t)ee * L::SZ + L::O_Q + v * NP + p];
+  {
+    int qofs[n];
+    bool qok[n];
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      const int r = tid + j * L::THREADS, ee = r / NP;
+      qofs[j] = ee * L::SZ + L::O_Q + r % NP;
+      qok[j] = ee < nel;
+    }
+    R* dst = rbar + (size_t)e0 * NP + tid;
+#pragma unroll 1
+    for (int v = 0; v < M; ++v, dst += (size_t)E * NP) {
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+        if (qok[j]) dst[j * L::THREADS] = sm[qofs[j] + v * NP];
+    }
   }
   // ---- face records [DIM][2][NF][C][E]: this thread owns the two ends of its
   // x-, y- and z-line, i.e. face node f = l of every face; consecutive lanes
@@ -643,6 +694,17 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
     const R* u0 = my + L::O_U0;
     // end nodes: x-line l (l n, l n + N), y-line l (by, by + N n), z-line l (l, l + N n^2)
     const int by = (l % n) + (l / n) * n * n;
+    if constexpr (PACK) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          fx.U[sd][v] = fxy.U[sd][v].v.x;
+          fx.F[sd][v] = fxy.F[sd][v].v.x;
+          fy.U[sd][v] = fxy.U[sd][PackXY<EQ>::rot(v)].v.y;
+          fy.F[sd][v] = fxy.F[sd][PackXY<EQ>::rot(v)].v.y;
+        }
+    }
     write_records<EQ, R, NF>(trace, fx, 0, E, e0 + el, l, u0 + l * n, u0 + l * n + N, NP);
     if constexpr (ONEQ) {
       FaceAcc<EQ, R> fyo;
