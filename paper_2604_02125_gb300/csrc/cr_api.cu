@@ -134,6 +134,7 @@ void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
     for (int q = 0; q < 6; ++q) {
       t64->D[p][q] = (p <= N && q <= N) ? D[p][q] : 0.0;
       t32->D[p][q] = (float)t64->D[p][q];
+      t32->D2f[p][q] = t64->D2f[p][q] = make_float2(2.0f * t32->D[p][q], 2.0f * t32->D[p][q]);
     }
     t64->w[p] = t32->w[p] = p <= N ? w[p] : 0.0;
   }

@@ -80,6 +80,10 @@ struct RefTab {
   double w[6];     // quadrature weights (FP64, diagnostics)
   R a[7][7], b[7]; // Butcher tableau of the degree (same values as rk_a / rk_b)
   signed char slot[7];   // register slot of a stage residual needed beyond the next stage, else -1
+  // (2 D_pq, 2 D_pq) in FP32: the coefficients of the packed FP32x2 pair loop
+  // as ready register pairs (measured 53.8 -> 52.5 us per volume launch, 2D
+  // Euler 256^2, N = 3, against forming them from D_pq in the loop)
+  float2 D2f[6][6];
 };
 
 // Step record of one solve.  The CFL reduction needs no fence and no

@@ -136,7 +136,7 @@ __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2
     for (int b = a + 1; b < n; ++b) {
       f2 f[M];
       EQ::two_point(0, q[a], q[b], f, pp);
-      const f2 dab(2.0f * tb.D[a][b]), dba(2.0f * tb.D[b][a]);
+      const f2 dab(tb.D2f[a][b]), dba(tb.D2f[b][a]);
 #pragma unroll
       for (int v = 0; v < M; ++v) { acc[a][v] += dab * f[v]; acc[b][v] += dba * f[v]; }
     }
@@ -145,8 +145,8 @@ __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2
   EQ::flux(0, q[N], fend[1], pp);
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    acc[0][v] += f2(2.0f * tb.D[0][0]) * fend[0][v];
-    acc[N][v] += f2(2.0f * tb.D[N][N]) * fend[1][v];
+    acc[0][v] += f2(tb.D2f[0][0]) * fend[0][v];
+    acc[N][v] += f2(tb.D2f[N][N]) * fend[1][v];
   }
 #pragma unroll
   for (int k = 0; k < n; ++k)
