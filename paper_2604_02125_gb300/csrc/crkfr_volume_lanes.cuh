@@ -232,9 +232,13 @@ struct FaceAcc : FaceAccNc<EQ, R> {
 
 // Register budget of the 2D Euler lane kernels of degree 4 and 5 (resident
 // CTAs per SM; measured: more CTAs outweigh the spills up to the shared-memory
-// limit) and the highest degree that takes the packed x/y form (above it both
-// lines' pair data no longer fit in the budget).
-constexpr int kMinB4 = 3, kMinB5 = 2, kPackMaxN = 3;
+// limit) and the highest degree that takes the packed x/y form.  Degree 4
+// packed runs at 2 CTAs per SM (168 registers, 108 B of spills): 99 against
+// 117 us per volume launch of the scalar form at 3 CTAs (2D Euler 128^2, FP32);
+// at 3 CTAs the packed form spilled 488 B (140 us).  At degree 5 both lines'
+// pair data no longer fit: packed 99 (2 CTAs) or 109 us (1 CTA) against 83 us
+// for the scalar form (96^2).
+constexpr int kMinB4 = 3, kMinB4Pack = 2, kMinB5 = 2, kPackMaxN = 4;
 // degree 2, FP32: short lines, little per-thread state; 8 CTAs per SM (measured
 // 0.50 -> 0.42 ms per batched volume launch against 3)
 constexpr int kMinB2 = 8;
@@ -269,7 +273,7 @@ struct LaneLayout<EQ, N, R, 0> {
   // lines' pair data at once)
   static constexpr int MINB = EQ::NC ? (2 * (bytes() + 1024) <= 228 * 1024 ? kMinBNc : 1)
                             : (THREADS <= 128) ? ((N == 2 && sizeof(R) == 4) ? kMinB2 : PACK ? 3 : 4)
-                            : (DIM == 2) ? (N == 4 ? kMinB4 : N == 5 ? kMinB5 : 1) : 1;
+                            : (DIM == 2) ? (N == 4 ? (PACK ? kMinB4Pack : kMinB4) : N == 5 ? kMinB5 : 1) : 1;
   static constexpr bool fits() { return bytes() <= 227 * 1024 && THREADS <= 1024; }
 };
 
