@@ -125,7 +125,7 @@ bool get_ops(int eq, int dim, int prec, int vol, int N, VariantOps* o, int ncflu
   return false;
 }
 
-void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
+void fill_ref_tables(int N, const MeshArgs& ma, RefTab<double>* t64, RefTab<float>* t32) {
   double xi[6], w[6], D[6][6];
   ref_tables(N, xi, w, D);
   std::memset(t64, 0, sizeof(*t64));
@@ -135,6 +135,8 @@ void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32) {
       t64->D[p][q] = (p <= N && q <= N) ? D[p][q] : 0.0;
       t32->D[p][q] = (float)t64->D[p][q];
       t32->D2f[p][q] = t64->D2f[p][q] = make_float2(2.0f * t32->D[p][q], 2.0f * t32->D[p][q]);
+      t32->D2s[p][q] = t64->D2s[p][q] =
+          make_float2(2.0f * t32->D[p][q] * ma.inv_dx_f[0], 2.0f * t32->D[p][q] * ma.inv_dx_f[1]);
     }
     t64->w[p] = t32->w[p] = p <= N ? w[p] : 0.0;
   }
@@ -220,7 +222,7 @@ void fill_launch_ctx(const cr_mesh_desc& d, const VariantOps& o, LaunchCtx* plc)
   lc.ma.c_h = d.c_h;
   lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
-  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
+  fill_ref_tables(d.degree_N, lc.ma, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
   int dev = 0;
   cudaGetDevice(&dev);

@@ -117,7 +117,7 @@ bool ops_mhd2s_fp32_central(int N, VariantOps* o);
 void ref_tables(int N, double* xi, double* w, double D[6][6]);
 
 // reference-element and tableau tables of degree N in both precisions
-void fill_ref_tables(int N, RefTab<double>* t64, RefTab<float>* t32);
+void fill_ref_tables(int N, const MeshArgs& ma, RefTab<double>* t64, RefTab<float>* t32);
 
 // launchers of a (system, dim, precision, degree) variant; false if none;
 // ncflux = CR_NCFLUX_STAGES selects the GLM-MHD kernels with the stage-wise

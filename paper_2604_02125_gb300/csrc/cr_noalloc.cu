@@ -123,7 +123,7 @@ extern "C" int cr_step_noalloc(const cr_mesh_desc* desc, const double* u_in, dou
   lc.ma.c_h = d.c_h;
   lc.pp64 = PhysParams<double>{d.gamma, 1.0 / (d.gamma - 1.0), d.c_h, d.vol};
   lc.pp32 = PhysParams<float>{(float)d.gamma, (float)(1.0 / (d.gamma - 1.0)), (float)d.c_h, d.vol};
-  fill_ref_tables(d.degree_N, &lc.tb64, &lc.tb32);
+  fill_ref_tables(d.degree_N, lc.ma, &lc.tb64, &lc.tb32);
   lc.epb = default_epb(o);
   lc.sms = 1;
   if ((e = cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return to_status(e);

@@ -159,7 +159,7 @@ k_step_fused(double* u, R* rbar, R* trace, DevState* st, unsigned* flags, const 
     }
     const unsigned tn = t + G;
     const Prefetch pf = (tn < ntiles && whole(tn)) ? pf_of(tn) : Prefetch{nullptr, 0, 0, nullptr, nullptr};
-    volume_lanes_tile<EQ, N, R, 0, 0>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
+    volume_lanes_tile<EQ, N, R, 0, 0, true>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
                                       staged ? staging : nullptr, pf);
     // publish: every thread's records and R-bar are visible device-wide
     // before the readiness value

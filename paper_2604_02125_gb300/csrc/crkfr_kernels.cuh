@@ -84,6 +84,11 @@ struct RefTab {
   // as ready register pairs (measured 53.8 -> 52.5 us per volume launch, 2D
   // Euler 256^2, N = 3, against forming them from D_pq in the loop)
   float2 D2f[6][6];
+  // (2 D_pq / dx, 2 D_pq / dy) of one solve: a single solve's packed pair loop
+  // folds the 1/dx scaling of its two lines into the coefficients (measured
+  // 52.7 -> 51.4 us per volume launch, 2D Euler 256^2, N = 3); the batched
+  // kernels, which share one table among solves of different sizes, scale
+  float2 D2s[6][6];
 };
 
 // Step record of one solve.  The CFL reduction needs no fence and no

@@ -121,7 +121,9 @@ __host__ __device__ constexpr int swap_xy(int c) {
   return c == 1 ? 2 : c == 2 ? 1 : (EQ::NC && c == 5) ? 6 : (EQ::NC && c == 6) ? 5 : c;
 }
 
-template <class EQ, int N>
+// PRE: the coefficients carry 1/dx of each line (RefTab::D2s), else the
+// residual is scaled at the end
+template <class EQ, int N, bool PRE>
 __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2 (&acc)[N + 1][EQ::M],
                                                  f2 (&fend)[2][EQ::M], const PhysParams<f2>& pp,
                                                  const RefTab<float>& tb, f2 inv_dx) {
@@ -136,7 +138,7 @@ __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2
     for (int b = a + 1; b < n; ++b) {
       f2 f[M];
       EQ::two_point(0, q[a], q[b], f, pp);
-      const f2 dab(tb.D2f[a][b]), dba(tb.D2f[b][a]);
+      const f2 dab(PRE ? tb.D2s[a][b] : tb.D2f[a][b]), dba(PRE ? tb.D2s[b][a] : tb.D2f[b][a]);
 #pragma unroll
       for (int v = 0; v < M; ++v) { acc[a][v] += dab * f[v]; acc[b][v] += dba * f[v]; }
     }
@@ -145,13 +147,15 @@ __device__ __forceinline__ void line_residual_xy(const f2 (&q)[N + 1][EQ::P], f2
   EQ::flux(0, q[N], fend[1], pp);
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    acc[0][v] += f2(tb.D2f[0][0]) * fend[0][v];
-    acc[N][v] += f2(tb.D2f[N][N]) * fend[1][v];
+    acc[0][v] += f2(PRE ? tb.D2s[0][0] : tb.D2f[0][0]) * fend[0][v];
+    acc[N][v] += f2(PRE ? tb.D2s[N][N] : tb.D2f[N][N]) * fend[1][v];
   }
+  if constexpr (!PRE) {
 #pragma unroll
-  for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k)
 #pragma unroll
-    for (int v = 0; v < M; ++v) acc[k][v] *= inv_dx;
+      for (int v = 0; v < M; ++v) acc[k][v] *= inv_dx;
+  }
 }
 
 
@@ -402,7 +406,9 @@ __device__ __forceinline__ void issue_prefetch(const Prefetch& pf) {
 // [var][32][NP] (the tile's slice of the global layout).  S1 = 1: a single
 // stage with b = 1 (R-bar = R(u), face records of u), the volume part of one
 // stage of the multi-stage RKFR step.
-template <class EQ, int N, typename R, int SH = 0, int S1 = 0>
+// PRE: a single solve's reference table (the packed pair loop's coefficients
+// carry 1/dx, RefTab::D2s); false for the batched kernels
+template <class EQ, int N, typename R, int SH = 0, int S1 = 0, bool PRE = false>
 __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, R* __restrict__ rbar,
                                                   R* __restrict__ trace, const DevState* __restrict__ st,
                                                   const MeshArgs& ma, const PhysParams<R>& pp, const RefTab<R>& tb,
@@ -554,7 +560,7 @@ __device__ __forceinline__ void volume_lanes_tile(const double* __restrict__ u, 
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < P; ++c) q2[k][c] = f2(q[k][c], qy[k][PackXY<EQ>::rot(c)]);
-        line_residual_xy<EQ, N>(q2, acc2, fe2, pp2, tb, f2(inv_dx_of<float>(ma, 0), inv_dx_of<float>(ma, 1)));
+        line_residual_xy<EQ, N, PRE>(q2, acc2, fe2, pp2, tb, f2(inv_dx_of<float>(ma, 0), inv_dx_of<float>(ma, 1)));
 #pragma unroll
         for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -791,7 +797,7 @@ __device__ __forceinline__ void volume_lanes_persistent(const double* __restrict
     }
     const unsigned tn = t + gridDim.x;
     const Prefetch pf = (tn < ntiles && whole(tn)) ? pf_of(tn) : Prefetch{nullptr, 0, 0, nullptr, nullptr};
-    volume_lanes_tile<EQ, N, R, 0, S1>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
+    volume_lanes_tile<EQ, N, R, 0, S1, true>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
                                        staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
   }

@@ -54,8 +54,11 @@ def test_batch_matches_single_solves(cr, prec):
             info = s.info()
         # the same kernels give the same result to round-off; where the
         # autotuner picked the alternative shape (the scalar instead of the
-        # packed FP32 form), the two are different FP32 evaluations
-        alt = tun["N%d_volume" % m["N"]]["shape"] != 0 and prec == "fp32"
+        # packed FP32 form), the two are different FP32 evaluations, and so
+        # are the packed forms themselves: a single solve's packed pair loop
+        # takes coefficients that carry its 1/dx, the batched one scales after
+        packed = m.get("eq", "euler") == "euler" and m["dim"] == 2 and m["N"] <= 4
+        alt = prec == "fp32" and (tun["N%d_volume" % m["N"]]["shape"] != 0 or packed)
         assert rel(outs[k], ref) <= (1e-6 if alt else 1e-14), (k, m["N"], rel(outs[k], ref))
         assert infos[k]["steps"] == 5 and abs(infos[k]["t"] - info["t"]) <= (1e-6 if alt else 1e-15) * info["t"]
 
