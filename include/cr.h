@@ -133,8 +133,8 @@ typedef struct cr_ctx cr_ctx;   /* opaque; owned by the library */
  * scratch, step records; CR_SCHEME_RKFR adds a stage state and s - 1 stage
  * increments, CR_NCFLUX_STAGES the stage traces after the face records,
  * CR_LIMITER_BLENDING a second state buffer -- the limited step reads u^n
- * from one and writes u^{n+1} to the other -- and one coefficient per
- * element).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
+ * from one and writes u^{n+1} to the other --, one coefficient and flag per
+ * element and the list of the elements the limiter touches).  Returns CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENODEV. */
 int cr_init_mesh(cr_ctx **out, const cr_mesh_desc *desc, int n_solves, void *cuda_stream);
 
 /* Caller-provided device memory.  cr_workspace_bytes stores in *bytes the

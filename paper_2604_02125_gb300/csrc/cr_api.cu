@@ -355,6 +355,8 @@ static void free_single(cr_ctx* c) {
     cudaFree(c->lc.araw);
     cudaFree(c->lc.alpha);
     cudaFree(c->lc.touched);
+    cudaFree(c->lc.tlist);
+    cudaFree(c->lc.tcount);
     cudaFree(c->lc.flags);
     cudaFree(c->lc.rbar);
     cudaFree(c->lc.trace);
@@ -367,6 +369,7 @@ static void free_single(cr_ctx* c) {
   c->lc.u = nullptr;
   c->lc.araw = c->lc.alpha = nullptr;
   c->lc.touched = nullptr;
+  c->lc.tlist = c->lc.tcount = nullptr;
   c->lc.flags = nullptr;
   c->lc.rbar = c->lc.trace = nullptr;
   c->lc.st = nullptr;
@@ -480,6 +483,8 @@ static int plan_single(cr_ctx* c, std::vector<BufSpec>* plan) {
     plan->push_back({(void**)&lc.araw, sizeof(double) * (size_t)E});
     plan->push_back({(void**)&lc.alpha, sizeof(double) * (size_t)E});
     plan->push_back({(void**)&lc.touched, (size_t)E});
+    plan->push_back({(void**)&lc.tlist, sizeof(unsigned) * (size_t)E});
+    plan->push_back({(void**)&lc.tcount, sizeof(unsigned)});
   }
   plan->push_back({&lc.rbar, o.real_bytes * (size_t)o.M * nodes});
   plan->push_back({&lc.trace, o.real_bytes * ((size_t)o.dim * 2 * o.C * NFt + o.ncs_per_elem * (size_t)E)});
@@ -531,6 +536,7 @@ static int init_single(cr_ctx* c, void* workspace = nullptr) {
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   e = cudaMemsetAsync(lc.st, 0, sizeof(DevState), c->stream);
   if (e == cudaSuccess && c->limited) e = cudaMemsetAsync(lc.alpha, 0, sizeof(double) * (size_t)E, c->stream);
+  if (e == cudaSuccess && c->limited) e = cudaMemsetAsync(lc.tcount, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess && c->fused) e = cudaMemsetAsync(lc.flags, 0, sizeof(unsigned) * (size_t)((E + 31) / 32), c->stream);
   if (e != cudaSuccess) { free_single(c); return cuda_status(e); }
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);

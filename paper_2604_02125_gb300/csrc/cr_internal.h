@@ -34,6 +34,8 @@ struct LaunchCtx {
   double* araw;
   double* alpha;      // smoothed coefficients
   unsigned char* touched;   // 1 where the limited step changes the element's update
+  unsigned* tlist;          // the touched elements, in no particular order
+  unsigned* tcount;         // their number (reset by the coefficient kernel)
   LimTab lt;
   // fused single-launch step: per-tile readiness values
   unsigned* flags;

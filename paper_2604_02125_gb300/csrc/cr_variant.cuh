@@ -123,8 +123,9 @@ struct Variant {
   static cudaError_t alpha(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (!EQ::NC) {
       const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
-      k_alpha_raw<EQ, N, R><<<grid, 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
-      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.ma);
+      k_alpha_raw<EQ, N, R><<<grid, 128, 0, s>>>(c.u, c.araw, c.tcount, c.ma, c.lt);
+      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.tlist,
+                                                                              c.tcount, c.ma);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -142,11 +143,13 @@ struct Variant {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
+      // over the touched elements' nodes (their number is known on the device
+      // only: a grid of four CTAs per SM strides over them), else over all nodes
       const long long total = c.ma.E * L::NP;
-      const unsigned grid = (unsigned)((total + 255) / 256);
+      const unsigned grid = (unsigned)std::min((total + 255) / 256, kFaceLanes ? 4LL * c.sms : (total + 255) / 256);
       k_face_update_limited<EQ, N, R><<<grid, 256, 0, s>>>(c.u, c.u_next, (const R*)c.rbar, (const R*)c.trace, c.alpha,
-                                                           c.touched, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.lt,
-                                                           c.slot, kFaceLanes ? 1 : 0);
+                                                           c.tlist, c.tcount, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c),
+                                                           c.lt, c.slot, kFaceLanes ? 1 : 0);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;

@@ -147,9 +147,13 @@ __device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long
 // ---------------------------------------------------------------------------
 template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(128)
-k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshArgs ma, const LimTab lt) {
+k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, unsigned* __restrict__ tcount, const MeshArgs ma,
+            const LimTab lt) {
   const long long E = ma.E;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // the touched list of this step starts empty (k_alpha_smooth fills it after
+  // this kernel; the last step's limited kernel has read it before)
+  if (e == 0) *tcount = 0u;
   if (e >= E) return;
   if constexpr (sizeof(R) == 4) {
     const float En = indicator_energy<EQ, N, float>(u, E, e, ma, lt);
@@ -168,17 +172,11 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, const MeshA
   araw[e] = fmin(a, lt.alpha_max);
 }
 
-// smoothed coefficient per element: max(raw_e, raw_nb / 2 over the face
-// neighbours); touched[e] = 1 where the limited step changes the element's
-// update: a raw coefficient above zero on the element, a face neighbour or a
-// face neighbour's face neighbour (the raw values are non-negative, so "above
-// zero" is "bits not all zero", tested with integer ORs)
+// one element of k_alpha_smooth; returns whether the limiter touches it
 template <int DIM>
-__global__ void __launch_bounds__(256)
-k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, unsigned char* __restrict__ touched,
-               const MeshArgs ma) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ma.E) return;
+__device__ __forceinline__ bool alpha_smooth_one(const double* __restrict__ araw, double* __restrict__ alpha,
+                                                      unsigned char* __restrict__ touched, const MeshArgs& ma,
+                                                      unsigned e) {
   const unsigned long long* rb = reinterpret_cast<const unsigned long long*>(araw);
   unsigned c[3] = {0, 0, 0};
   elem_coords<DIM>((unsigned)e, ma, c);
@@ -201,6 +199,31 @@ k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, unsi
     }
   alpha[e] = a;
   touched[e] = any != 0ull ? 1 : 0;
+  return any != 0ull;
+}
+
+// smoothed coefficient per element: max(raw_e, raw_nb / 2 over the face
+// neighbours); touched[e] = 1 where the limited step changes the element's
+// update: a raw coefficient above zero on the element, a face neighbour or a
+// face neighbour's face neighbour (the raw values are non-negative, so "above
+// zero" is "bits not all zero", tested with integer ORs).  The touched
+// elements are also appended to tlist (one atomic per warp), so that the
+// per-node limited kernel runs over them alone.
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_alpha_smooth(const double* __restrict__ araw, double* __restrict__ alpha, unsigned char* __restrict__ touched,
+               unsigned* __restrict__ tlist, unsigned* __restrict__ tcount, const MeshArgs ma) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool t = e < ma.E && alpha_smooth_one<DIM>(araw, alpha, touched, ma, (unsigned)e);
+  // warp-aggregated append (every lane of the warp takes part)
+  const unsigned mask = __ballot_sync(0xffffffffu, t);
+  if (mask) {
+    const int lane = threadIdx.x & 31, lead = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == lead) base = atomicAdd(tcount, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (t) tlist[base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)e;
+  }
 }
 
 // u^n of node p of element e in the path's arithmetic
@@ -329,17 +352,19 @@ template <class EQ, int N, typename R>
 __global__ void __launch_bounds__(256)
 k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout, const R* __restrict__ rbar,
                       const R* __restrict__ trace, const double* __restrict__ alpha,
-                      const unsigned char* __restrict__ touched, DevState* __restrict__ st, const MeshArgs ma,
-                      const PhysParams<R> pp, const RefTab<R> tb, const LimTab lt, int slot, int only_touched) {
+                      const unsigned* __restrict__ tlist, const unsigned* __restrict__ tcount,
+                      DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                      const LimTab lt, int slot, int only_touched) {
   constexpr int DIM = EQ::DIM, M = EQ::M, n = N + 1, NP = ipow(n, DIM), NF = NP / n;
   constexpr bool F32 = sizeof(R) == 4;
   const long long E = ma.E;
   if (st->status & ST_TIMEOUT) return;
-  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
   R lam = R(0);
   bool bad = false;
-  const unsigned e = gid / NP;
-  if (gid < (unsigned)(E * NP) && !(only_touched && !touched[e])) {
+  // nodes of the touched elements (only_touched), else of every element
+  const unsigned total = (only_touched ? *tcount : (unsigned)E) * (unsigned)NP;
+  for (unsigned gid = blockIdx.x * blockDim.x + threadIdx.x; gid < total; gid += gridDim.x * blockDim.x) {
+    const unsigned e = only_touched ? tlist[gid / NP] : gid / NP;
     const int p = (int)(gid % NP);
     unsigned ec[3] = {0, 0, 0};
     elem_coords<DIM>(e, ma, ec);
@@ -409,7 +434,9 @@ k_face_update_limited(const double* __restrict__ uin, double* __restrict__ uout,
       else uu[v] = uin[g] + du;
       uout[g] = uu[v];
     }
-    bad = !physical_state<EQ, R>(uu, ma, lam);
+    R lamn = R(0);
+    bad = !physical_state<EQ, R>(uu, ma, lamn) || bad;
+    lam = fmax(lam, lamn);
   }
   reduce_lambda<R>(lam, bad, st, slot ^ 1);
 }

@@ -190,7 +190,8 @@ def test_random_descriptors_rejected_without_gpu(lib):
 def test_workspace_bytes_without_gpu(lib):
     """cr_workspace_bytes follows the documented buffer list (no CUDA call):
     the state, R-bar, face records, step record and totals of the plain
-    step; a second state buffer and per-element coefficients with the limiter;
+    step; a second state buffer, per-element coefficients and flags and the
+    list of touched elements with the limiter;
     the stage state and s - 1 stage increments with the multi-stage scheme.
     cr_init_mesh_ws rejects a NULL, misaligned or too small workspace before
     any CUDA call."""
@@ -206,7 +207,7 @@ def test_workspace_bytes_without_gpu(lib):
         plain = (al(8 * M * nodes) + al(R * M * nodes) + al(R * 2 * 2 * (2 * M + 1) * NF * E) + al(step_record)
                  + al(8 * ((nodes + 255) // 256) * (M + 2)))
         assert crkfr.workspace_bytes(mesh, prec) == plain
-        lim = plain + al(8 * M * nodes) + al(8 * E) + al(8 * E) + al(E)
+        lim = plain + al(8 * M * nodes) + al(8 * E) + al(8 * E) + al(E) + al(4 * E) + al(4)
         assert crkfr.workspace_bytes(dict(mesh, limiter=True), prec) == lim
         rk = plain + al(8 * M * nodes) + al(R * 3 * M * nodes)
         assert crkfr.workspace_bytes(mesh, prec, scheme="rkfr") == rk
