@@ -122,8 +122,9 @@ struct Variant {
   }
   static cudaError_t alpha(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (!EQ::NC) {
-      const unsigned grid = (unsigned)((c.ma.E + 127) / 128);
-      k_alpha_raw<EQ, N, R><<<grid, 128, 0, s>>>(c.u, c.araw, c.tcount, c.ma, c.lt);
+      constexpr int T = AlphaRawLayout<EQ, N, R>::THREADS;
+      const unsigned grid = (unsigned)((c.ma.E + T - 1) / T);
+      k_alpha_raw<EQ, N, R><<<grid, T, 0, s>>>(c.u, c.araw, c.tcount, c.ma, c.lt);
       k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.tlist,
                                                                               c.tcount, c.ma);
       return cudaGetLastError();

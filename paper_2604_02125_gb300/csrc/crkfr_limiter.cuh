@@ -36,6 +36,8 @@
 // first-order fluxes read neighbouring nodes of other elements), so a limited
 // context ping-pongs between two buffers.
 #pragma once
+#include <type_traits>
+
 #include "crkfr_kernels.cuh"
 
 namespace crk {
@@ -53,37 +55,16 @@ struct LimTab {
   float tau_f, sharp_f, alpha_max_f, e_lo_f, e_hi_f;
 };
 
-// Energy fraction of the highest modes of one element's rho p (see
-// k_alpha_raw).  FP64: E = max((T - T1)/T, (T1 - T2)/T1) from the three sums;
-// FP32: the top and second-top energies summed directly (sums of squares, no
-// cancellation), E = max(Ttop/T, Tsec/(T - Ttop)).
-template <class EQ, int N, typename T>
-__device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long long E, long long e,
-                                              const MeshArgs& ma, const LimTab& lt) {
+
+// The energy fraction of one element from its rho p node values, load(p) for
+// node p (the values stay in this function's registers).
+template <class EQ, int N, typename T, class Load>
+__device__ __forceinline__ T indicator_of_values(Load load, const LimTab& lt) {
   constexpr int DIM = EQ::DIM, n = N + 1, NP = ipow(n, DIM);
   constexpr bool F32 = sizeof(T) == 4;
   T m[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    T rho, Et, mm = T(0);
-    if constexpr (F32) {
-      rho = d2f_int(u[(size_t)e * NP + p]);
-      Et = d2f_int(u[((size_t)(DIM + 1) * E + e) * NP + p]);
-    } else {
-      rho = u[(size_t)e * NP + p];
-      Et = u[((size_t)(DIM + 1) * E + e) * NP + p];
-    }
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      T mk;
-      if constexpr (F32) mk = d2f_int(u[((size_t)(1 + k) * E + e) * NP + p]);
-      else mk = u[((size_t)(1 + k) * E + e) * NP + p];
-      mm += mk * mk;
-    }
-    // rho p = (gamma - 1)(rho E - |m|^2 / 2)
-    const T gm1 = F32 ? T(ma.gamma_f - 1.0f) : T(ma.gamma - 1.0);
-    m[p] = gm1 * (rho * Et - T(0.5) * mm);
-  }
+  for (int p = 0; p < NP; ++p) m[p] = load(p);
   // modal coefficients: the 1D transform along every direction in turn (fully
   // unrolled: compile-time indices keep the element's values in registers)
 #pragma unroll
@@ -137,6 +118,49 @@ __device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long
   return En;
 }
 
+// Energy fraction of the highest modes of one element's rho p (see
+// k_alpha_raw).  FP64: E = max((T - T1)/T, (T1 - T2)/T1) from the three sums;
+// FP32: the top and second-top energies summed directly (sums of squares, no
+// cancellation), E = max(Ttop/T, Tsec/(T - Ttop)).
+template <class EQ, int N, typename T>
+__device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long long E, long long e,
+                                              const MeshArgs& ma, const LimTab& lt) {
+  constexpr int DIM = EQ::DIM, NP = ipow(N + 1, DIM);
+  constexpr bool F32 = sizeof(T) == 4;
+  return indicator_of_values<EQ, N, T>([&](int p) {
+    T rho, Et, mm = T(0);
+    if constexpr (F32) {
+      rho = d2f_int(u[(size_t)e * NP + p]);
+      Et = d2f_int(u[((size_t)(DIM + 1) * E + e) * NP + p]);
+    } else {
+      rho = u[(size_t)e * NP + p];
+      Et = u[((size_t)(DIM + 1) * E + e) * NP + p];
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      T mk;
+      if constexpr (F32) mk = d2f_int(u[((size_t)(1 + k) * E + e) * NP + p]);
+      else mk = u[((size_t)(1 + k) * E + e) * NP + p];
+      mm += mk * mk;
+    }
+    // rho p = (gamma - 1)(rho E - |m|^2 / 2)
+    const T gm1 = F32 ? T(ma.gamma_f - 1.0f) : T(ma.gamma - 1.0);
+    return gm1 * (rho * Et - T(0.5) * mm);
+  }, lt);
+}
+
+// Elements per block of k_alpha_raw (one thread each) when their rho p values
+// fit the static shared memory (48 KB), else 0: every thread reads its own
+// element's values from global memory.
+template <class EQ, int N, typename R>
+struct AlphaRawLayout {
+  using T = typename std::conditional<sizeof(R) == 4, float, double>::type;
+  static constexpr int NP = ipow(N + 1, EQ::DIM);
+  static constexpr int FIT = 49152 / (int)((NP + 1) * sizeof(T)) / 32 * 32;
+  static constexpr int EB = FIT >= 128 ? 128 : FIT >= 32 ? FIT : 0;
+  static constexpr int THREADS = EB > 0 ? EB : 128;
+};
+
 // ---------------------------------------------------------------------------
 // Blending coefficient per element before smoothing.  The FP64 form evaluates
 // it in FP64 throughout.  The FP32 form evaluates the energy fraction in FP32
@@ -146,17 +170,54 @@ __device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long
 // FP32 differs from the FP64 one by about 1e-6.
 // ---------------------------------------------------------------------------
 template <class EQ, int N, typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(AlphaRawLayout<EQ, N, R>::THREADS)
 k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, unsigned* __restrict__ tcount, const MeshArgs ma,
             const LimTab lt) {
+  constexpr int DIM = EQ::DIM, NP = ipow(N + 1, DIM), EB = AlphaRawLayout<EQ, N, R>::EB;
+  using T = typename AlphaRawLayout<EQ, N, R>::T;
   const long long E = ma.E;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   // the touched list of this step starts empty (k_alpha_smooth fills it after
   // this kernel; the last step's limited kernel has read it before)
   if (e == 0) *tcount = 0u;
+  const T* row = nullptr;
+  if constexpr (EB > 0) {
+    // rho p of the block's EB elements through shared memory: coalesced loads
+    // of the block's contiguous slice of every variable, one row of NP + 1
+    // values per element (no bank conflicts when each thread reads its row)
+    __shared__ T s_m[EB > 0 ? EB * (NP + 1) : 1];
+    const long long e0 = (long long)blockIdx.x * EB;
+    const int nel = (int)min((long long)EB, E - e0);
+    const size_t vs = (size_t)E * NP;
+    const T gm1 = sizeof(T) == 4 ? T(ma.gamma_f - 1.0f) : T(ma.gamma - 1.0);
+    for (int r = threadIdx.x; r < nel * NP; r += EB) {
+      const size_t g = (size_t)e0 * NP + r;
+      T rho, Et, mm = T(0);
+      if constexpr (sizeof(T) == 4) {
+        rho = d2f_int(u[g]);
+        Et = d2f_int(u[(DIM + 1) * vs + g]);
+      } else {
+        rho = u[g];
+        Et = u[(DIM + 1) * vs + g];
+      }
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        T mk;
+        if constexpr (sizeof(T) == 4) mk = d2f_int(u[(1 + k) * vs + g]);
+        else mk = u[(1 + k) * vs + g];
+        mm += mk * mk;
+      }
+      s_m[(r / NP) * (NP + 1) + r % NP] = gm1 * (rho * Et - T(0.5) * mm);
+    }
+    __syncthreads();
+    row = s_m + threadIdx.x * (NP + 1);
+  }
+  auto from_row = [&](int p) { return row[p]; };
   if (e >= E) return;
   if constexpr (sizeof(R) == 4) {
-    const float En = indicator_energy<EQ, N, float>(u, E, e, ma, lt);
+    float En;
+    if constexpr (EB > 0) En = indicator_of_values<EQ, N, float>(from_row, lt);
+    else En = indicator_energy<EQ, N, float>(u, E, e, ma, lt);
     const bool near = fabsf(En - lt.e_lo_f) <= 0.02f * lt.e_lo_f || fabsf(En - lt.e_hi_f) <= 0.02f * lt.e_hi_f;
     if (!near) {
       float a = En < lt.e_lo_f ? 0.0f : En > lt.e_hi_f ? 1.0f
@@ -165,7 +226,9 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, unsigned* _
       return;
     }
   }
-  const double En = indicator_energy<EQ, N, double>(u, E, e, ma, lt);
+  double En;
+  if constexpr (sizeof(R) == 8 && EB > 0) En = indicator_of_values<EQ, N, double>(from_row, lt);
+  else En = indicator_energy<EQ, N, double>(u, E, e, ma, lt);
   double a = 1.0 / (1.0 + exp(-(lt.sharp / lt.tau) * (En - lt.tau)));
   if (a < 0.001) a = 0.0;
   if (a > 0.999) a = 1.0;
