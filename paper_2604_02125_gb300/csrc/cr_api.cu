@@ -397,7 +397,12 @@ static int launch_step(cr_ctx* c, cudaStream_t s, int parity) {
     // update kernel from the parity's buffer into the other one
     c->lc.u = state_buf(c, parity);
     c->lc.u_next = state_buf(c, parity ^ 1);
-    if (c->desc[0].prec == CR_FP32_PAIRFLUX) {
+    if (c->ops.volume_ind) {
+      // FP32 lane form: the volume kernel evaluates the raw coefficients of
+      // the tiles it has finished, then the smoothing pass
+      CR_TRY(c->ops.volume_ind(c->lc, s));
+      CR_TRY(c->ops.alpha_smooth(c->lc, s));
+    } else if (c->desc[0].prec == CR_FP32_PAIRFLUX) {
       // FP32 form: the FP64 indicator beside the FP32 volume kernel
       // (measured 0.164 -> 0.155 ms per step at 256^2, N = 3)
       CR_TRY(cudaEventRecord(c->ev_fork, s));
@@ -783,11 +788,17 @@ int cr_time_kernels(cr_ctx* c, int nsteps, void* flush_buf, size_t flush_bytes, 
     for (int j = 0; j < S && rc == CR_OK; ++j) {
       cudaEvent_t* e4 = &ev[4 * ((size_t)k * S + j)];
       cudaEventRecord(e4[0], c->stream);
-      // limiter: the coefficient kernel counts with the volume kernel
-      cudaError_t e = c->limited ? c->ops.alpha(c->lc, c->stream) : cudaSuccess;
-      if (e == cudaSuccess)
-        e = rk ? c->ops.volume_stage(c->lc, c->stream, j == 0 ? c->lc.u : c->lc.ustage, j == 0)
-               : c->ops.volume(c->lc, c->stream);
+      // limiter: the coefficient kernels count with the volume kernel
+      cudaError_t e = cudaSuccess;
+      if (c->limited && c->ops.volume_ind) {
+        e = c->ops.volume_ind(c->lc, c->stream);
+        if (e == cudaSuccess) e = c->ops.alpha_smooth(c->lc, c->stream);
+      } else {
+        if (c->limited) e = c->ops.alpha(c->lc, c->stream);
+        if (e == cudaSuccess)
+          e = rk ? c->ops.volume_stage(c->lc, c->stream, j == 0 ? c->lc.u : c->lc.ustage, j == 0)
+                 : c->ops.volume(c->lc, c->stream);
+      }
       if (e != cudaSuccess) rc = CR_ECUDA;
       cudaEventRecord(e4[1], c->stream);
       cudaEventRecord(e4[2], c->stream);

@@ -73,6 +73,10 @@ struct VariantOps {
   // the limited face / update kernel from u into u_next
   cudaError_t (*alpha)(const LaunchCtx&, cudaStream_t);
   cudaError_t (*face_limited)(const LaunchCtx&, cudaStream_t);
+  // FP32 lane form: the volume kernel that also evaluates the raw
+  // coefficients of u, then the smoothing pass alone (null elsewhere)
+  cudaError_t (*volume_ind)(const LaunchCtx&, cudaStream_t);
+  cudaError_t (*alpha_smooth)(const LaunchCtx&, cudaStream_t);
   // the whole step in one cooperative persistent launch (lane forms of the
   // single-stage scheme; null where the layouts do not allow it); phase 0..2
   cudaError_t (*step_fused)(const LaunchCtx&, cudaStream_t, int phase);

@@ -120,6 +120,35 @@ struct Variant {
     }
     return cudaGetLastError();
   }
+  static constexpr bool kVolInd = kLanes && !EQ::NC && sizeof(R) == 4;
+  static cudaError_t volume_ind(const LaunchCtx& c, cudaStream_t s) {
+    if constexpr (kVolInd) {
+      static int occ = -1;
+      if (occ < 0) {
+        int nb = 0;
+        cudaFuncSetAttribute(k_volume_lanes_ind<EQ, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PL::bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_volume_lanes_ind<EQ, N, R>, LL::THREADS, PL::bytes());
+        occ = nb > 0 ? nb : 1;
+      }
+      const long long ntiles = (c.ma.E + 31) / 32;
+      const long long grid = std::min(ntiles, (long long)c.sms * occ);
+      k_volume_lanes_ind<EQ, N, R><<<(unsigned)grid, LL::THREADS, PL::bytes(), s>>>(
+          c.u, (R*)c.rbar, (R*)c.trace, c.st, c.ma, PP<R>::get(c), PP<R>::tab(c), c.slot, c.araw, c.tcount, c.lt);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
+  static cudaError_t alpha_smooth(const LaunchCtx& c, cudaStream_t s) {
+    if constexpr (!EQ::NC) {
+      if constexpr (kVolInd)
+        k_alpha_fix<EQ, N><<<(unsigned)((c.ma.E + 127) / 128), 128, 0, s>>>(c.u, c.araw, c.ma, c.lt);
+      k_alpha_smooth<EQ::DIM><<<(unsigned)((c.ma.E + 255) / 256), 256, 0, s>>>(c.araw, c.alpha, c.touched, c.tlist,
+                                                                              c.tcount, c.ma);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
   static cudaError_t alpha(const LaunchCtx& c, cudaStream_t s) {
     if constexpr (!EQ::NC) {
       constexpr int T = AlphaRawLayout<EQ, N, R>::THREADS;
@@ -305,6 +334,8 @@ struct Variant {
     o->step_fused = kFused ? &step_fused : nullptr;
     o->alpha = EQ::NC ? nullptr : &alpha;
     o->face_limited = EQ::NC ? nullptr : &face_limited;
+    o->volume_ind = kVolInd ? &volume_ind : nullptr;
+    o->alpha_smooth = EQ::NC ? nullptr : &alpha_smooth;
     o->totals = &totals;
     o->set_smem = &set_smem;
   }

@@ -149,6 +149,37 @@ __device__ __forceinline__ T indicator_energy(const double* __restrict__ u, long
   }, lt);
 }
 
+// FP32 form: the raw coefficient of an FP32 energy fraction, or -1 where it
+// lies within 2% of a clip threshold (the FP64 evaluation decides there).
+__device__ __forceinline__ float alpha_of_energy_f32(float En, const LimTab& lt) {
+  const bool near = fabsf(En - lt.e_lo_f) <= 0.02f * lt.e_lo_f || fabsf(En - lt.e_hi_f) <= 0.02f * lt.e_hi_f;
+  if (near) return -1.0f;
+  const float a = En < lt.e_lo_f ? 0.0f : En > lt.e_hi_f ? 1.0f
+                                  : 1.0f / (1.0f + expf(-(lt.sharp_f / lt.tau_f) * (En - lt.tau_f)));
+  return fminf(a, lt.alpha_max_f);
+}
+
+// The raw coefficient in FP64 from u^n in global memory (the FP32 form's
+// elements near a clip threshold).
+template <class EQ, int N>
+__device__ __forceinline__ double alpha_raw_fp64(const double* __restrict__ u, long long E, long long e,
+                                              const MeshArgs& ma, const LimTab& lt) {
+  const double En = indicator_energy<EQ, N, double>(u, E, e, ma, lt);
+  double a = 1.0 / (1.0 + exp(-(lt.sharp / lt.tau) * (En - lt.tau)));
+  if (a < 0.001) a = 0.0;
+  if (a > 0.999) a = 1.0;
+  return fmin(a, lt.alpha_max);
+}
+
+// The FP64 evaluation of the raw coefficients the FP32 volume kernel left
+// at -1 (near a clip threshold).
+template <class EQ, int N>
+__global__ void __launch_bounds__(128)
+k_alpha_fix(const double* __restrict__ u, double* __restrict__ araw, const MeshArgs ma, const LimTab lt) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ma.E && araw[e] < 0.0) araw[e] = alpha_raw_fp64<EQ, N>(u, ma.E, e, ma, lt);
+}
+
 // Elements per block of k_alpha_raw (one thread each) when their rho p values
 // fit the static shared memory (48 KB), else 0: every thread reads its own
 // element's values from global memory.
@@ -218,11 +249,9 @@ k_alpha_raw(const double* __restrict__ u, double* __restrict__ araw, unsigned* _
     float En;
     if constexpr (EB > 0) En = indicator_of_values<EQ, N, float>(from_row, lt);
     else En = indicator_energy<EQ, N, float>(u, E, e, ma, lt);
-    const bool near = fabsf(En - lt.e_lo_f) <= 0.02f * lt.e_lo_f || fabsf(En - lt.e_hi_f) <= 0.02f * lt.e_hi_f;
-    if (!near) {
-      float a = En < lt.e_lo_f ? 0.0f : En > lt.e_hi_f ? 1.0f
-                                       : 1.0f / (1.0f + expf(-(lt.sharp_f / lt.tau_f) * (En - lt.tau_f)));
-      araw[e] = f2d_int(fminf(a, lt.alpha_max_f));
+    const float a = alpha_of_energy_f32(En, lt);
+    if (a >= 0.0f) {
+      araw[e] = f2d_int(a);
       return;
     }
   }

@@ -31,6 +31,7 @@
 
 #include "crkfr_f2.cuh"
 #include "crkfr_kernels.cuh"
+#include "crkfr_limiter.cuh"
 
 namespace crk {
 
@@ -753,11 +754,18 @@ struct PersistLayout {
 // u^n of whole tiles arrives by TMA bulk copy one tile ahead.  first = false
 // (later stages of a multi-stage RKFR step) takes the dt the step's first
 // launch recorded.
-template <class EQ, int N, typename R, int S1>
+struct NoTileWork {
+  __device__ void operator()(long long, const float*) const {}
+};
+
+// after_tile(e0, sm): more work on a finished tile whose u^n is still in the
+// lane layout's u^n region of sm (the rest of the layout is free)
+template <class EQ, int N, typename R, int S1, class After = NoTileWork>
 __device__ __forceinline__ void volume_lanes_persistent(const double* __restrict__ u, R* __restrict__ rbar,
                                                         R* __restrict__ trace, DevState* __restrict__ st,
                                                         const MeshArgs& ma, const PhysParams<R>& pp,
-                                                        const RefTab<R>& tb, int slot, bool first) {
+                                                        const RefTab<R>& tb, int slot, bool first,
+                                                        After after_tile = After{}) {
   using PL = PersistLayout<EQ, N, R>;
   constexpr int M = EQ::M, NP = LaneLayout<EQ, N, R>::NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -800,6 +808,10 @@ __device__ __forceinline__ void volume_lanes_persistent(const double* __restrict
     volume_lanes_tile<EQ, N, R, 0, S1, true>(u, rbar, trace, st, ma, pp, tb, (long long)t * 32, dtR, sm,
                                        staged ? staging : nullptr, pf);
     __syncthreads();   // shared memory is reused by the next tile
+    if constexpr (!std::is_same<After, NoTileWork>::value) {
+      after_tile((long long)t * 32, reinterpret_cast<const float*>(sm));
+      __syncthreads();
+    }
   }
 }
 
@@ -809,6 +821,53 @@ k_volume_lanes(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict
                DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
                int slot) {
   volume_lanes_persistent<EQ, N, R, 0>(u, rbar, trace, st, ma, pp, tb, slot, true);
+}
+
+// The volume kernel of the limited FP32 step, which also evaluates the
+// limiter's raw coefficients of every tile it has finished: rho p at the nodes
+// from the tile's FP32 u^n (the same values k_alpha_raw converts), staged in
+// the pair-data region, then one lane per element takes the energy fraction
+// and the coefficient; near a clip threshold it leaves -1 for k_alpha_fix's
+// FP64 evaluation (measured: the FP64 evaluation here stalled the tile on
+// fronts, 110.2 against 108.5 us per step).  It also empties the touched list
+// for k_alpha_smooth.
+template <class EQ, int N, typename R>
+__global__ void __launch_bounds__(LaneLayout<EQ, N, R>::THREADS, LaneLayout<EQ, N, R>::MINB)
+k_volume_lanes_ind(const double* __restrict__ u, R* __restrict__ rbar, R* __restrict__ trace,
+                   DevState* __restrict__ st, const MeshArgs ma, const PhysParams<R> pp, const RefTab<R> tb,
+                   int slot, double* __restrict__ araw, unsigned* __restrict__ tcount, const LimTab lt) {
+  static_assert(sizeof(R) == 4 && !EQ::NC, "the FP32 Euler form");
+  using L = LaneLayout<EQ, N, R>;
+  constexpr int DIM = EQ::DIM, n = N + 1, NP = L::NP;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *tcount = 0u;
+  auto indicator = [&](long long e0, const float* sm) {
+    float* smw = const_cast<float*>(sm);
+    const int tid = threadIdx.x, l = tid >> 5, el = tid & 31;
+    const int nel = (int)min(32LL, ma.E - e0);
+    float* my = smw + (size_t)el * L::SZ;
+    if (el < nel) {
+      const float gm1 = ma.gamma_f - 1.0f;
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        const int p = l * n + k;
+        const float rho = my[L::O_U0 + p], Et = my[L::O_U0 + (DIM + 1) * NP + p];
+        float mm = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const float mk = my[L::O_U0 + (1 + d) * NP + p];
+          mm += mk * mk;
+        }
+        my[L::O_Q + p] = gm1 * (rho * Et - 0.5f * mm);
+      }
+    }
+    __syncthreads();
+    if (tid < 32 && el < nel) {
+      const float En = indicator_of_values<EQ, N, float>([&](int p) { return my[L::O_Q + p]; }, lt);
+      const float a = alpha_of_energy_f32(En, lt);
+      araw[e0 + el] = a >= 0.0f ? f2d_int(a) : -1.0;   // k_alpha_fix takes it in FP64
+    }
+  };
+  volume_lanes_persistent<EQ, N, R, 0>(u, rbar, trace, st, ma, pp, tb, slot, true, indicator);
 }
 
 // volume part of one RKFR stage (input: the stage state)
